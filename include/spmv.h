@@ -1,0 +1,238 @@
+/*
+ * spmv.h -- C ABI of the GB300 (sm_103a) FP64 sparse matrix-vector library.
+ *
+ * The library computes y = A x for a sparse M x N matrix A held in one of the
+ * five representations compared in arXiv:1805.11938 (CSR, CSR5, ELL,
+ * SELL-C-sigma and HYB = ELL + COO), converts between CSR and each of them,
+ * extracts static matrix features, and picks a format per matrix with a small
+ * learned classifier, as the paper's Sec. V proposes.
+ *
+ * Conventions for every call
+ *  - Pointers named *_dev, x, y and the spmv_csr arrays are DEVICE pointers of
+ *    the current CUDA device; *_host pointers are host memory.
+ *  - Indices are int32, values FP64.  Row pointers (ptr) are int32 with
+ *    ptr[0] = 0 and ptr[M] = nnz, so nnz < 2^31.
+ *  - Every call returns SPMV_OK (0) or a negative spmv_status.  A call that
+ *    fails writes nothing to its outputs (y, handles, ...).
+ *    spmv_last_error() gives a one-line detail of the calling thread's last
+ *    failure.
+ *  - Work is enqueued on the caller's stream and runs asynchronously; only
+ *    the calls documented as synchronising wait for the device.
+ *  - Handles and models own their device memory; inputs, x and y stay owned
+ *    by the caller.  x and y must not alias.
+ */
+#ifndef SPMV_GB300_H
+#define SPMV_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#if defined(__GNUC__)
+#define SPMV_API __attribute__((visibility("default")))
+#else
+#define SPMV_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The five representations of Sec. II-B (Table I), in the paper's order. */
+typedef enum {
+    SPMV_CSR = 0,
+    SPMV_CSR5 = 1,
+    SPMV_ELL = 2,
+    SPMV_SELL = 3, /* SELL-C-sigma; sigma = 1 is plain SELL */
+    SPMV_HYB = 4
+} spmv_fmt;
+
+#define SPMV_NUM_FORMATS 5
+#define SPMV_NUM_FEATURES 16
+#define SPMV_MLP_PARAMS 5573 /* 16x64 + 64 + 64x64 + 64 + 64x5 + 5 */
+
+typedef enum {
+    SPMV_OK = 0,
+    SPMV_ERR_INVALID_ARG = -1,    /* null pointer, bad size, malformed CSR, bad parameter */
+    SPMV_ERR_INDEX_OVERFLOW = -2, /* a count or padded size does not fit the index type */
+    SPMV_ERR_TOO_LARGE = -3,      /* padded footprint above spmv_params.max_bytes */
+    SPMV_ERR_CUDA = -4,           /* a CUDA runtime call failed (detail in spmv_last_error) */
+    SPMV_ERR_NO_MODEL = -5,       /* spmv_select without a model */
+    SPMV_ERR_ALLOC = -6,          /* device allocation failed */
+    SPMV_ERR_WRONG_FORMAT = -7    /* call not valid for this handle's format */
+} spmv_status;
+
+/* A CSR matrix in device memory (Sec. II-B "CSR"): ptr[M+1], idx[nnz],
+ * val[nnz].  Columns need not be sorted within a row; duplicates are kept and
+ * summed by every product.  The caller keeps the arrays alive for the duration
+ * of the call that receives them (convert copies what it needs). */
+typedef struct {
+    int32_t m, n;
+    int64_t nnz;
+    const int32_t* ptr;
+    const int32_t* idx;
+    const double* val;
+} spmv_csr;
+
+/* Tuning parameters.  A zero field means "choose automatically".  The
+ * paper names them: CSR5 tile width omega and height sigma (Sec. II-B "CSR5"),
+ * SELL slice height C and sorting scope sigma (Sec. II-B "SELL"), and the HYB
+ * ELL width K (Sec. II-B "HYB"). */
+typedef struct {
+    int32_t sell_C;        /* SELL slice height: 32, 64 or 128 rows (0 -> 32) */
+    int32_t sell_sigma;    /* SELL sorting window in rows: 1 (plain SELL), a multiple of sell_C,
+                              or -1 for the whole matrix (0 -> 32 * sell_C) */
+    int32_t csr5_omega;    /* CSR5 tile width: 32, the warp width, is the only value (0 -> 32) */
+    int32_t csr5_sigma;    /* CSR5 tile height, 1..32 (0 -> 16) */
+    int32_t csr_block_nnz; /* CSR row-block nonzero budget, a power of two in [128, 4096] (0 -> 1024) */
+    int32_t hyb_k;         /* HYB ELL width: > 0 explicit, 0 -> the typical-length rule,
+                              SPMV_HYB_K_NONE -> every entry in the COO part */
+    int64_t max_bytes;     /* cap on the handle's device footprint (0 -> 90% of free memory) */
+} spmv_params;
+
+#define SPMV_HYB_K_NONE (-1)
+#define SPMV_SELL_SIGMA_ALL (-1)
+
+typedef struct spmv_handle spmv_handle;
+typedef struct spmv_model spmv_model;
+typedef struct spmv_batch spmv_batch;
+
+/* What a handle holds, after automatic choices are resolved. */
+typedef struct {
+    int32_t fmt, m, n;
+    int64_t nnz;
+    int64_t device_bytes;   /* memory owned by the handle */
+    int64_t stored_slots;   /* value slots stored, padding included */
+    spmv_params params;     /* resolved tuning parameters (hyb_k: the K used) */
+    int64_t aux[4];         /* format detail: CSR units, CSR5 tiles, ELL K, SELL slices,
+                               HYB tail entries; see spmv_handle_array for the arrays */
+} spmv_info;
+
+/* ---------------------------------------------------------------- basics */
+
+SPMV_API int spmv_version(void);
+SPMV_API const char* spmv_strerror(int status);
+/* One-line detail of the calling thread's last failed call ("" if none). */
+SPMV_API const char* spmv_last_error(void);
+
+/* -------------------------------------------------------- conversion, run */
+
+/* Build a handle holding A in format `fmt` (Sec. II-B layouts; Sec. III-D and
+ * Algorithm 1 convert once and then multiply many times).  The CSR input is
+ * validated on the device first (ptr[0] = 0, ptr non-decreasing, ptr[M] = nnz,
+ * 0 <= idx < N); a violation returns SPMV_ERR_INVALID_ARG.  params may be
+ * NULL (all automatic).  Synchronises `stream` (it reads sizes back).
+ * The handle owns copies of everything it needs; free it with spmv_free.
+ * Errors: INVALID_ARG, INDEX_OVERFLOW (padded slots >= 2^31 where an int32
+ * offset is needed), TOO_LARGE (footprint > max_bytes), ALLOC, CUDA. */
+SPMV_API int spmv_convert(spmv_fmt fmt, const spmv_csr* csr, const spmv_params* params, cudaStream_t stream,
+                 spmv_handle** out);
+
+/* y = A x (Sec. II-A), y overwritten (beta = 0).  x holds N doubles and y M
+ * doubles, both device memory.  Asynchronous on `stream`; no host sync.
+ * Launches the format's kernels (one to three launches). */
+SPMV_API int spmv_run(const spmv_handle* h, const double* x, double* y, cudaStream_t stream);
+
+/* Write A back as CSR (ptr[M+1], idx[nnz], val[nnz], device, caller-owned).
+ * The round trip is exact: same ptr, same column order within each row, same
+ * value bits (explicit zeros, -0.0 and duplicates included).  Asynchronous. */
+SPMV_API int spmv_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, cudaStream_t stream);
+
+SPMV_API int spmv_handle_info(const spmv_handle* h, spmv_info* out);
+
+/* Device pointer and element count of one of the handle's arrays, by name,
+ * for inspection (e.g. "tile_ptr", "flags", "y_off", "seg_off", "tile_idx",
+ * "tile_val", "empty_ptr", "empty_rows", "row_len", "col", "val", "perm",
+ * "slice_ptr", "tail_rows", "tail_ptr", "tail_col", "tail_val", "units",
+ * "ptr", "idx").  The memory stays owned by the handle.  Returns
+ * INVALID_ARG for a name the format does not have. */
+SPMV_API int spmv_handle_array(const spmv_handle* h, const char* name, const void** dev_ptr, int64_t* count,
+                      int32_t* elem_bytes);
+
+SPMV_API void spmv_free(spmv_handle* h);
+
+/* ------------------------------------------------- features and selection */
+
+/* The 16 static features of Sec. V-B (Table IV's eight plus eight more) as
+ * float32 into feat_dev[16]; see the feature definitions in the library's
+ * documentation.  One kernel launch, asynchronous.  Rows are sampled (at most
+ * 16384) so the cost does not grow with M. */
+SPMV_API int spmv_features(const spmv_csr* csr, float* feat_dev, cudaStream_t stream);
+
+/* A trained selector: network parameters (SPMV_MLP_PARAMS floats, W1, b1, W2,
+ * b2, W3, b3 row-major) and the per-feature minimum and maximum of the
+ * transformed training features (Sec. V-B "Feature Scaling"), host arrays
+ * copied to the device. */
+SPMV_API int spmv_model_create(const float* params_host, const float* lo_host, const float* hi_host, spmv_model** out);
+SPMV_API void spmv_model_free(spmv_model* m);
+
+/* Features + scaling + network + argmax in one launch (Sec. V-A deployment:
+ * features in, representation label out).  Writes the format id to
+ * fmt_dev[0] and, if logits_dev is not NULL, the 5 logits.  Asynchronous. */
+SPMV_API int spmv_select_async(const spmv_csr* csr, const spmv_model* model, int32_t* fmt_dev, float* logits_dev,
+                      cudaStream_t stream);
+
+/* As spmv_select_async, then waits for `stream` and returns the id in *out. */
+SPMV_API int spmv_select(const spmv_csr* csr, const spmv_model* model, cudaStream_t stream, spmv_fmt* out);
+
+/* --------------------------------------------------- selector training */
+
+/* Sec. V-B "Feature Scaling" on the device: X[b][j] = clamp((t_j - lo_j) /
+ * (hi_j - lo_j), 0, 1), t the transformed feature (log2(1+f) for sizes and
+ * counts, -log2(max(f, 2^-60)) for nnz_frac), 0 where hi_j == lo_j.
+ * feat_dev and X_dev are B x 16 row-major; lo/hi are device float[16]. */
+SPMV_API int spmv_mlp_scale(const float* feat_dev, const float* lo_dev, const float* hi_dev, int32_t B, float* X_dev,
+                   cudaStream_t stream);
+
+/* Mean cross-entropy over B samples and its gradient with respect to all
+ * SPMV_MLP_PARAMS parameters (one CTA, deterministic).  X_dev is B x 16,
+ * labels_dev B ints in [0, 5).  loss_dev may be NULL. */
+SPMV_API int spmv_mlp_loss_grad(const float* theta_dev, const float* X_dev, const int32_t* labels_dev, int32_t B,
+                       float* grad_dev, float* loss_dev, cudaStream_t stream);
+
+/* One Adam step (step number t >= 1) on n parameters, in place. */
+SPMV_API int spmv_mlp_adam(float* theta_dev, const float* grad_dev, float* m_dev, float* v_dev, int32_t n, int32_t t,
+                  float lr, float beta1, float beta2, float eps, cudaStream_t stream);
+
+/* `steps` full-batch Adam steps (numbered t0+1 ... t0+steps) in one launch;
+ * loss_hist_dev (may be NULL) receives each step's loss. */
+SPMV_API int spmv_mlp_train(float* theta_dev, float* m_dev, float* v_dev, const float* X_dev, const int32_t* labels_dev,
+                   int32_t B, int32_t steps, int32_t t0, float lr, float beta1, float beta2, float eps,
+                   float* loss_hist_dev, cudaStream_t stream);
+
+/* Logits (B x 5, may be NULL) and argmax labels (may be NULL). */
+SPMV_API int spmv_mlp_forward(const float* theta_dev, const float* X_dev, int32_t B, float* logits_dev,
+                     int32_t* pred_dev, cudaStream_t stream);
+
+/* ------------------------------------------------------------- batching */
+
+/* Many independent products y_b = A_b x_b in one persistent launch.  build
+ * lays out a work list over all handles (each keeps its own format) and
+ * captures the launch in a CUDA graph on `stream`; the handles must outlive
+ * the batch.  Synchronises `stream`. */
+SPMV_API int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t stream, spmv_batch** out);
+
+/* xs_host[b] / ys_host[b]: device pointers of x_b and y_b (host arrays of
+ * `count` pointers).  Uploads them when they differ from the previous call,
+ * then replays the graph.  Asynchronous. */
+SPMV_API int spmv_batch_run(spmv_batch* b, const double* const* xs_host, double* const* ys_host, cudaStream_t stream);
+
+/* The same products as `count` ordinary per-matrix spmv_run launches,
+ * captured once in their own CUDA graph and replayed (the comparison point). */
+SPMV_API int spmv_batch_run_separate(spmv_batch* b, const double* const* xs_host, double* const* ys_host,
+                            cudaStream_t stream);
+
+SPMV_API void spmv_batch_free(spmv_batch* b);
+
+/* --------------------------------------------------------- fault testing */
+
+/* Make the k-th device allocation from now fail with SPMV_ERR_ALLOC
+ * (k >= 1; 0 disables).  For testing error paths; process-wide. */
+SPMV_API void spmv_debug_fail_alloc(int32_t k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMV_GB300_H */

@@ -1,0 +1,350 @@
+// Batched SpMV: many independent products y_b = A_b x_b, each matrix in its
+// own format, in one persistent launch (plus a second one for the passes that
+// must follow the first: CSR5 carry calibration and the HYB COO tail).
+//
+// The work list is built once on the host from the handles' unit counts:
+// task = {matrix, kind, index}.  A grid of (SMs x resident blocks) 256-thread
+// blocks takes tasks from an atomic counter until the list is exhausted (no
+// block ever waits on another).  build captures
+//     memset(counters) -> phase 1 -> phase 2
+// into a CUDA graph; run uploads the x/y pointer tables when they change and
+// replays the graph.
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace spmv {
+
+enum TaskKind : int32_t {
+    T_CSR = 0,       // one CSR unit (block)
+    T_CSR5 = 1,      // 8 CSR5 tiles (warp each)
+    T_ELL = 2,       // 512 ELL rows
+    T_ELL_LONG = 3,  // one long ELL row
+    T_SELL = 4,      // 8 SELL units (warp each)
+    T_CSR5_CAL = 5,  // 256 tiles of calibration / empty rows
+    T_HYB_TAIL = 6   // one HYB tail unit (block), adds into y
+};
+
+struct MatDesc {
+    int32_t fmt, sell_r;
+    int32_t n_zero;
+    int32_t ell_nb;
+    const int32_t* zero_rows;
+    const int32_t* long_rows;
+    dev::CsrArgs csr;   // CSR, or the HYB tail (ADD)
+    dev::Csr5Args csr5;
+    dev::EllArgs ell;   // ELL, or the ELL part of HYB
+    dev::SellArgs sell;
+};
+
+struct BatchDev {
+    const MatDesc* mats;
+    const int4* tasks;
+    int32_t n_tasks;
+    unsigned* counter;
+    const double* const* xs;
+    double* const* ys;
+};
+
+__global__ void __launch_bounds__(256) k_batch(BatchDev B) {
+    extern __shared__ double prod[];
+    __shared__ double red[8];
+    __shared__ int flag;
+    __shared__ int task_sh;
+    for (;;) {
+        if (threadIdx.x == 0) task_sh = (int)atomicAdd(B.counter, 1u);
+        __syncthreads();
+        const int ti = task_sh;
+        __syncthreads();
+        if (ti >= B.n_tasks) break;
+        const int4 t = B.tasks[ti];
+        const MatDesc& md = B.mats[t.x];
+        const double* x = B.xs[t.x];
+        double* y = B.ys[t.x];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        switch (t.y) {
+            case T_CSR: {
+                dev::CsrArgs a = md.csr;
+                a.x = x;
+                a.y = y;
+                dev::csr_unit<false>(a, t.z, prod, red, &flag);
+                break;
+            }
+            case T_HYB_TAIL: {
+                dev::CsrArgs a = md.csr;
+                a.x = x;
+                a.y = y;
+                dev::csr_unit<true>(a, t.z, prod, red, &flag);
+                break;
+            }
+            case T_CSR5: {
+                dev::Csr5Args a = md.csr5;
+                a.x = x;
+                a.y = y;
+                const int64_t tile = (int64_t)t.z * 8 + warp;
+                if (tile < a.ntiles) dev::csr5_tile(a, tile, lane);
+                break;
+            }
+            case T_CSR5_CAL: {
+                dev::Csr5Args a = md.csr5;
+                a.x = x;
+                a.y = y;
+                dev::csr5_calibrate(a, (int64_t)t.z * 256 + threadIdx.x, md.zero_rows, md.n_zero);
+                break;
+            }
+            case T_ELL: {
+                dev::EllArgs a = md.ell;
+                a.x = x;
+                a.y = y;
+                dev::ell_rows2(a, t.z * 512 + threadIdx.x * 2);
+                break;
+            }
+            case T_ELL_LONG: {
+                dev::EllArgs a = md.ell;
+                a.x = x;
+                a.y = y;
+                dev::ell_long_row(a, md.long_rows[t.z], red);
+                break;
+            }
+            case T_SELL: {
+                dev::SellArgs a = md.sell;
+                a.x = x;
+                a.y = y;
+                const int32_t u = t.z * 8 + warp;
+                if (u < t.w) {
+                    if (md.sell_r == 1) dev::sell_unit<1>(a, u, lane);
+                    else if (md.sell_r == 2) dev::sell_unit<2>(a, u, lane);
+                    else dev::sell_unit<4>(a, u, lane);
+                }
+                break;
+            }
+            default: break;
+        }
+    }
+}
+
+}  // namespace spmv
+
+struct spmv_batch {
+    int32_t count = 0;
+    std::vector<spmv_handle*> handles;
+    spmv::MatDesc* d_mats = nullptr;
+    int4* d_tasks1 = nullptr;
+    int4* d_tasks2 = nullptr;
+    int32_t n1 = 0, n2 = 0;
+    unsigned* d_counters = nullptr;  // 2
+    const double** d_xs = nullptr;
+    double** d_ys = nullptr;
+    std::vector<const double*> xs;
+    std::vector<double*> ys;
+    size_t smem = 0;
+    int grid = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphExec_t exec_sep = nullptr;
+    std::vector<const double*> sep_xs;
+    std::vector<double*> sep_ys;
+    ~spmv_batch() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (exec_sep) cudaGraphExecDestroy(exec_sep);
+        if (cap) cudaStreamDestroy(cap);
+        spmv::dev_free(d_mats);
+        spmv::dev_free(d_tasks1);
+        spmv::dev_free(d_tasks2);
+        spmv::dev_free(d_counters);
+        spmv::dev_free(d_xs);
+        spmv::dev_free(d_ys);
+    }
+};
+
+namespace spmv {
+
+static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, std::vector<int4>& t2, int32_t b,
+                      int32_t& max_block_nnz) {
+    memset(&d, 0, sizeof d);
+    d.fmt = h->fmt;
+    switch (h->fmt) {
+        case SPMV_CSR:
+            d.csr = dev::CsrArgs{h->cu.units, h->ptr, h->idx, h->val, nullptr, nullptr, nullptr, h->cu.partial,
+                                 h->cu.counters, h->cu.chunk};
+            if (h->cu.block_nnz > max_block_nnz) max_block_nnz = h->cu.block_nnz;
+            for (int32_t u = 0; u < h->cu.n; ++u) t1.push_back(make_int4(b, T_CSR, u, 0));
+            break;
+        case SPMV_CSR5: {
+            d.csr5 = dev::Csr5Args{h->ptr, h->tile_ptr, h->flags, h->tile_idx, h->tile_val, h->empty_ptr, h->empty_rows,
+                                   h->carry, h->nnz, h->ntiles, h->csr5_sigma, nullptr, nullptr};
+            d.zero_rows = h->zero_rows;
+            d.n_zero = h->n_zero_rows;
+            const int64_t g1 = ceil_div(h->ntiles, 8);
+            for (int64_t g = 0; g < g1; ++g) t1.push_back(make_int4(b, T_CSR5, (int32_t)g, 0));
+            const int64_t n2 = h->ntiles > h->n_zero_rows ? h->ntiles : h->n_zero_rows;
+            for (int64_t g = 0; g < ceil_div(n2, 256); ++g) t2.push_back(make_int4(b, T_CSR5_CAL, (int32_t)g, 0));
+            break;
+        }
+        case SPMV_ELL:
+        case SPMV_HYB: {
+            const int32_t long_len = h->fmt == SPMV_ELL ? (int32_t)h->aux[2] : 0x7fffffff;
+            d.ell = dev::EllArgs{h->ell.row_len, h->ell.col, h->ell.val, h->ell.ld, h->m, long_len, nullptr, nullptr};
+            d.long_rows = h->ell.long_rows;
+            d.ell_nb = (int32_t)ceil_div(h->m, 512);
+            for (int32_t g = 0; g < d.ell_nb; ++g) t1.push_back(make_int4(b, T_ELL, g, 0));
+            if (h->fmt == SPMV_ELL)
+                for (int32_t j = 0; j < h->ell.n_long; ++j) t1.push_back(make_int4(b, T_ELL_LONG, j, 0));
+            if (h->fmt == SPMV_HYB && h->n_tail_rows > 0) {
+                d.csr = dev::CsrArgs{h->tail_units.units, h->tail_ptr, h->tail_col, h->tail_val, h->tail_rows, nullptr,
+                                     nullptr, h->tail_units.partial, h->tail_units.counters, h->tail_units.chunk};
+                if (h->tail_units.block_nnz > max_block_nnz) max_block_nnz = h->tail_units.block_nnz;
+                for (int32_t u = 0; u < h->tail_units.n; ++u) t2.push_back(make_int4(b, T_HYB_TAIL, u, 0));
+            }
+            break;
+        }
+        case SPMV_SELL:
+            d.sell = dev::SellArgs{h->sell_units, h->slice_ptr, h->sell_len, h->perm, h->sell_col, h->sell_val,
+                                   h->sell_partial, h->sell_counters, h->m, kSellUnitWidth, nullptr, nullptr};
+            d.sell_r = h->sell_C / 32;
+            for (int64_t g = 0; g < ceil_div(h->n_sell_units, 8); ++g)
+                t1.push_back(make_int4(b, T_SELL, (int32_t)g, h->n_sell_units));
+            break;
+    }
+}
+
+static int capture_batch(spmv_batch* bt) {
+    cudaGraph_t g = nullptr;
+    SPMV_CUDA(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
+    cudaMemsetAsync(bt->d_counters, 0, 2 * sizeof(unsigned), bt->cap);
+    BatchDev a1{bt->d_mats, bt->d_tasks1, bt->n1, bt->d_counters, bt->d_xs, bt->d_ys};
+    if (bt->n1 > 0) k_batch<<<bt->grid, 256, bt->smem, bt->cap>>>(a1);
+    BatchDev a2{bt->d_mats, bt->d_tasks2, bt->n2, bt->d_counters + 1, bt->d_xs, bt->d_ys};
+    if (bt->n2 > 0) k_batch<<<bt->grid, 256, bt->smem, bt->cap>>>(a2);
+    cudaError_t e = cudaStreamEndCapture(bt->cap, &g);
+    if (e != cudaSuccess) return cuda_error(e, "batch graph capture");
+    e = cudaGraphInstantiate(&bt->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_error(e, "batch graph instantiate");
+    return SPMV_OK;
+}
+
+static int capture_separate(spmv_batch* bt) {
+    if (bt->exec_sep) {
+        cudaGraphExecDestroy(bt->exec_sep);
+        bt->exec_sep = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    SPMV_CUDA(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
+    int st = SPMV_OK;
+    for (int32_t b = 0; b < bt->count && st == SPMV_OK; ++b)
+        st = spmv_run(bt->handles[b], bt->sep_xs[b], bt->sep_ys[b], bt->cap);
+    cudaError_t e = cudaStreamEndCapture(bt->cap, &g);
+    if (st != SPMV_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_error(e, "separate graph capture");
+    e = cudaGraphInstantiate(&bt->exec_sep, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_error(e, "separate graph instantiate");
+    return SPMV_OK;
+}
+
+}  // namespace spmv
+
+using namespace spmv;
+
+extern "C" {
+
+int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t stream, spmv_batch** out) {
+    if (!handles || count <= 0 || !out) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    *out = nullptr;
+    for (int32_t b = 0; b < count; ++b)
+        if (!handles[b]) return set_error(SPMV_ERR_INVALID_ARG, "handle %d is NULL", b);
+    spmv_batch* bt = new spmv_batch();
+    bt->count = count;
+    bt->handles.assign(handles, handles + count);
+    std::vector<MatDesc> mats(count);
+    std::vector<int4> t1, t2;
+    int32_t max_bnnz = 128;
+    for (int32_t b = 0; b < count; ++b) fill_desc(handles[b], mats[b], t1, t2, b, max_bnnz);
+    bt->n1 = (int32_t)t1.size();
+    bt->n2 = (int32_t)t2.size();
+    bt->smem = sizeof(double) * 2 * (size_t)max_bnnz;
+    int st = dev_malloc((void**)&bt->d_mats, sizeof(MatDesc) * count);
+    if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_tasks1, sizeof(int4) * (t1.size() + 1));
+    if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_tasks2, sizeof(int4) * (t2.size() + 1));
+    if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_counters, 2 * sizeof(unsigned));
+    if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_xs, sizeof(double*) * count);
+    if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_ys, sizeof(double*) * count);
+    if (st != SPMV_OK) {
+        delete bt;
+        return st;
+    }
+    cudaError_t e = cudaMemcpy(bt->d_mats, mats.data(), sizeof(MatDesc) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !t1.empty())
+        e = cudaMemcpy(bt->d_tasks1, t1.data(), sizeof(int4) * t1.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !t2.empty())
+        e = cudaMemcpy(bt->d_tasks2, t2.data(), sizeof(int4) * t2.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(bt->d_xs, 0, sizeof(double*) * count);
+    if (e == cudaSuccess) e = cudaMemset(bt->d_ys, 0, sizeof(double*) * count);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && bt->smem > 48 * 1024)
+        e = cudaFuncSetAttribute((const void*)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 256, bt->smem);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete bt;
+        return cuda_error(e, "spmv_batch_build");
+    }
+    bt->grid = sms * (per_sm > 0 ? per_sm : 1);
+    bt->xs.assign(count, nullptr);
+    bt->ys.assign(count, nullptr);
+    st = capture_batch(bt);
+    if (st != SPMV_OK) {
+        delete bt;
+        return st;
+    }
+    (void)stream;
+    *out = bt;
+    return SPMV_OK;
+}
+
+static int upload_vectors(spmv_batch* bt, const double* const* xs, double* const* ys, cudaStream_t stream) {
+    bool same = true;
+    for (int32_t b = 0; b < bt->count && same; ++b) same = bt->xs[b] == xs[b] && bt->ys[b] == ys[b];
+    if (same) return SPMV_OK;
+    for (int32_t b = 0; b < bt->count; ++b) {
+        if (!xs[b] || !ys[b]) return set_error(SPMV_ERR_INVALID_ARG, "x or y of matrix %d is NULL", b);
+        bt->xs[b] = xs[b];
+        bt->ys[b] = ys[b];
+    }
+    SPMV_CUDA(cudaMemcpyAsync(bt->d_xs, bt->xs.data(), sizeof(double*) * bt->count, cudaMemcpyHostToDevice, stream));
+    SPMV_CUDA(cudaMemcpyAsync(bt->d_ys, bt->ys.data(), sizeof(double*) * bt->count, cudaMemcpyHostToDevice, stream));
+    SPMV_CUDA(cudaStreamSynchronize(stream));  // the host tables are reused on the next call
+    return SPMV_OK;
+}
+
+int spmv_batch_run(spmv_batch* bt, const double* const* xs, double* const* ys, cudaStream_t stream) {
+    if (!bt || !xs || !ys) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    SPMV_TRY(upload_vectors(bt, xs, ys, stream));
+    SPMV_CUDA(cudaGraphLaunch(bt->exec, stream));
+    return SPMV_OK;
+}
+
+int spmv_batch_run_separate(spmv_batch* bt, const double* const* xs, double* const* ys, cudaStream_t stream) {
+    if (!bt || !xs || !ys) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    bool same = bt->exec_sep != nullptr && (int32_t)bt->sep_xs.size() == bt->count;
+    for (int32_t b = 0; b < bt->count && same; ++b) same = bt->sep_xs[b] == xs[b] && bt->sep_ys[b] == ys[b];
+    if (!same) {
+        bt->sep_xs.assign(xs, xs + bt->count);
+        bt->sep_ys.assign(ys, ys + bt->count);
+        SPMV_TRY(capture_separate(bt));
+    }
+    SPMV_CUDA(cudaGraphLaunch(bt->exec_sep, stream));
+    return SPMV_OK;
+}
+
+void spmv_batch_free(spmv_batch* bt) { delete bt; }
+
+}  // extern "C"

@@ -1,0 +1,616 @@
+// Matrix features (Sec. V-B "Features", Table IV), their scaling (Sec. V-B
+// "Feature Scaling") and the selector network (Sec. V-A/V-B: features in,
+// representation label out; here a 16-64-64-5 multilayer perceptron, one of
+// the alternatives of Sec. V-D), with its training kernels.
+//
+// Feature definitions (rows sampled when M > 16384):
+//   R = all rows, or rows floor(k*M/16384) for k < 16384; len_i = ptr[i+1]-ptr[i]
+//   0 n_rows  1 n_cols  2 nnz/(M*N)  3 min len  4 max len  5 nnz/M
+//   6 std of len over R  7 std/mean  8 log2(max(nnz,1))  9 mean/max
+//  10 HYB tail fraction with K from R (lengths capped at 512)
+//  11 mean |col-row| and 12 max |col-row| over the first 64 entries of each sampled row
+//  13 fraction of empty rows  14 fraction of rows with len >= 32
+//  15 SELL-32 fill over R sorted, lengths capped at 512
+//
+// The features kernel is one cluster of 8 CTAs x 1024 threads: each CTA
+// reduces its share of the sampled rows, then CTA 0 combines the eight
+// partial results through distributed shared memory (no global scratch, no
+// atomics across CTAs) and, for selection, runs the network.
+#include <cooperative_groups.h>
+
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace cg = cooperative_groups;
+
+struct spmv_model {
+    float* params = nullptr;  // SPMV_MLP_PARAMS
+    float* lo = nullptr;      // 16
+    float* hi = nullptr;      // 16
+};
+
+namespace spmv {
+
+constexpr int kFeatCtas = 8;
+constexpr int kFeatThreads = 1024;
+constexpr int kSample = 16384;
+constexpr int kLenCap = 512;
+constexpr int kSpread = 64;
+
+// parameter offsets inside the flat vector
+constexpr int oW1 = 0, oB1 = 1024, oW2 = 1088, oB2 = 5184, oW3 = 5248, oB3 = 5568, kNP = 5573;
+
+struct FeatPart {
+    unsigned long long sum_len, sum_sq, spread_sum, spread_cnt;
+    int min_len, max_len, band;
+    unsigned empty, longc;
+    unsigned hist[kLenCap + 1];
+};
+
+__device__ __forceinline__ double feat_transform(int j, double f) {
+    if (j == 0 || j == 1 || j == 3 || j == 4 || j == 5 || j == 6 || j == 11 || j == 12) return log2(1.0 + f);
+    if (j == 2) return -log2(fmax(f, 0x1.0p-60));
+    return f;
+}
+
+__device__ __forceinline__ float feat_scale(int j, float f, const float* lo, const float* hi) {
+    const double t = feat_transform(j, (double)f);
+    const double span = (double)hi[j] - (double)lo[j];
+    if (!(span > 0.0)) return 0.0f;
+    double x = (t - (double)lo[j]) / span;
+    x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
+    return (float)x;
+}
+
+// 16 -> 64 -> 64 -> 5 forward for one sample by the first 64 threads of a block.
+// xs: 16 floats (shared), h1, h2: 64 floats (shared), z: 5 floats (shared).
+__device__ void mlp_forward_block(const float* __restrict__ th, const float* xs, float* h1, float* h2, float* z) {
+    const int j = threadIdx.x;
+    if (j < 64) {
+        float a = th[oB1 + j];
+        for (int i = 0; i < 16; ++i) a = fmaf(xs[i], th[oW1 + i * 64 + j], a);
+        h1[j] = a > 0.f ? a : 0.f;
+    }
+    __syncthreads();
+    if (j < 64) {
+        float a = th[oB2 + j];
+        for (int i = 0; i < 64; ++i) a = fmaf(h1[i], th[oW2 + i * 64 + j], a);
+        h2[j] = a > 0.f ? a : 0.f;
+    }
+    __syncthreads();
+    if (j < 5) {
+        float a = th[oB3 + j];
+        for (int i = 0; i < 64; ++i) a = fmaf(h2[i], th[oW3 + i * 5 + j], a);
+        z[j] = a;
+    }
+    __syncthreads();
+}
+
+__global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads)
+    k_features(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t m, int32_t n,
+               float* __restrict__ feat_out, const float* __restrict__ model_params, const float* __restrict__ lo,
+               const float* __restrict__ hi, int32_t* __restrict__ fmt_out, float* __restrict__ logits_out) {
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ FeatPart part;
+    __shared__ unsigned long long red_u[32][4];
+    __shared__ int red_i[32][3];
+    __shared__ unsigned red_c[32][2];
+    const int tid = threadIdx.x;
+    for (int b = tid; b <= kLenCap; b += kFeatThreads) part.hist[b] = 0;
+    __syncthreads();
+
+    const int64_t S = m < kSample ? m : kSample;
+    unsigned long long sl = 0, sq = 0, ssum = 0, scnt = 0;
+    int mn = 0x7fffffff, mx = 0, band = 0;
+    unsigned emp = 0, lng = 0;
+    const int64_t gt = (int64_t)cluster.block_rank() * kFeatThreads + tid;
+    for (int64_t k = gt; k < S; k += (int64_t)kFeatCtas * kFeatThreads) {
+        const int64_t i = (k * (int64_t)m) / S;
+        const int32_t p0 = ptr[i];
+        const int32_t len = ptr[i + 1] - p0;
+        sl += (unsigned long long)len;
+        sq += (unsigned long long)len * (unsigned long long)len;
+        mn = min(mn, len);
+        mx = max(mx, len);
+        emp += len == 0;
+        lng += len >= 32;
+        atomicAdd(&part.hist[len < kLenCap ? len : kLenCap], 1u);
+        const int ne = len < kSpread ? len : kSpread;
+        for (int e = 0; e < ne; ++e) {
+            const int64_t d = (int64_t)__ldg(idx + p0 + e) - i;
+            const int ad = (int)(d < 0 ? -d : d);
+            ssum += (unsigned long long)ad;
+            band = max(band, ad);
+        }
+        scnt += (unsigned long long)ne;
+    }
+    // block reduction (warp shuffles, then warp 0)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sl += __shfl_xor_sync(dev::kFull, sl, o);
+        sq += __shfl_xor_sync(dev::kFull, sq, o);
+        ssum += __shfl_xor_sync(dev::kFull, ssum, o);
+        scnt += __shfl_xor_sync(dev::kFull, scnt, o);
+        mn = min(mn, __shfl_xor_sync(dev::kFull, mn, o));
+        mx = max(mx, __shfl_xor_sync(dev::kFull, mx, o));
+        band = max(band, __shfl_xor_sync(dev::kFull, band, o));
+        emp += __shfl_xor_sync(dev::kFull, emp, o);
+        lng += __shfl_xor_sync(dev::kFull, lng, o);
+    }
+    const int w = tid >> 5, l = tid & 31;
+    if (l == 0) {
+        red_u[w][0] = sl; red_u[w][1] = sq; red_u[w][2] = ssum; red_u[w][3] = scnt;
+        red_i[w][0] = mn; red_i[w][1] = mx; red_i[w][2] = band;
+        red_c[w][0] = emp; red_c[w][1] = lng;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        FeatPart& p = part;
+        p.sum_len = p.sum_sq = p.spread_sum = p.spread_cnt = 0;
+        p.min_len = 0x7fffffff; p.max_len = 0; p.band = 0; p.empty = 0; p.longc = 0;
+        for (int i = 0; i < 32; ++i) {
+            p.sum_len += red_u[i][0]; p.sum_sq += red_u[i][1]; p.spread_sum += red_u[i][2]; p.spread_cnt += red_u[i][3];
+            p.min_len = min(p.min_len, red_i[i][0]); p.max_len = max(p.max_len, red_i[i][1]); p.band = max(p.band, red_i[i][2]);
+            p.empty += red_c[i][0]; p.longc += red_c[i][1];
+        }
+    }
+    cluster.sync();
+
+    if (cluster.block_rank() == 0) {
+        __shared__ unsigned hist[kLenCap + 1];
+        __shared__ unsigned ck[kLenCap + 2];
+        __shared__ FeatPart tot;
+        __shared__ float fs[16], xs[16], h1[64], h2[64], z[5];
+        __shared__ int Ksh;
+        __shared__ unsigned long long widths;
+        __shared__ unsigned long long upto_k;
+        if (tid == 0) {
+            tot.sum_len = tot.sum_sq = tot.spread_sum = tot.spread_cnt = 0;
+            tot.min_len = 0x7fffffff; tot.max_len = 0; tot.band = 0; tot.empty = 0; tot.longc = 0;
+            for (int r = 0; r < kFeatCtas; ++r) {
+                const FeatPart* q = cluster.map_shared_rank(&part, r);
+                tot.sum_len += q->sum_len; tot.sum_sq += q->sum_sq;
+                tot.spread_sum += q->spread_sum; tot.spread_cnt += q->spread_cnt;
+                tot.min_len = min(tot.min_len, q->min_len); tot.max_len = max(tot.max_len, q->max_len);
+                tot.band = max(tot.band, q->band); tot.empty += q->empty; tot.longc += q->longc;
+            }
+            Ksh = 0; widths = 0; upto_k = 0;
+        }
+        for (int b = tid; b <= kLenCap; b += kFeatThreads) {
+            unsigned s = 0;
+            for (int r = 0; r < kFeatCtas; ++r) s += cluster.map_shared_rank(&part, r)->hist[b];
+            hist[b] = s;
+        }
+        __syncthreads();
+        // c_k = #{len >= k}: suffix sums of the capped histogram (one thread per k, short loops)
+        for (int k = tid; k <= kLenCap; k += kFeatThreads) {
+            unsigned s = 0;
+            for (int b = k; b <= kLenCap; ++b) s += hist[b];
+            ck[k] = s;
+        }
+        __syncthreads();
+        const unsigned cnt = (unsigned)S;
+        const unsigned need = (cnt + 2) / 3;
+        // K = #{k in [1, 512] : c_k >= need}; SELL widths = sum_k ceil(c_k / 32)
+        int okK = 0;
+        unsigned long long wpart = 0;
+        if (tid >= 1 && tid <= kLenCap) {
+            okK = ck[tid] >= need;
+            wpart = (ck[tid] + 31) / 32;
+        }
+        okK = __syncthreads_count(okK);
+        atomicAdd(&widths, wpart);
+        __syncthreads();
+        if (tid == 0) Ksh = okK;
+        __syncthreads();
+        if (tid >= 1 && tid <= Ksh) atomicAdd(&upto_k, (unsigned long long)ck[tid]);  // sum_{k<=K} c_k = sum min(len, K)
+        __syncthreads();
+        if (tid == 0) {
+            const double L = (double)tot.sum_len;
+            const double mean = L / (double)cnt;
+            // std = sqrt(cnt * sum_sq - L^2) / cnt in exact 128-bit integer arithmetic
+            const unsigned long long a_lo = (unsigned long long)cnt * tot.sum_sq;
+            const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, tot.sum_sq);
+            const unsigned long long b_lo = tot.sum_len * tot.sum_len;
+            const unsigned long long b_hi = __umul64hi(tot.sum_len, tot.sum_len);
+            const unsigned long long d_lo = a_lo - b_lo;
+            const unsigned long long d_hi = a_hi - b_hi - (a_lo < b_lo ? 1ull : 0ull);
+            const double var_num = (double)d_hi * 18446744073709551616.0 + (double)d_lo;
+            const double sd = sqrt(var_num) / (double)cnt;
+            const double nnz = (double)ptr[m];
+            const unsigned long long tail = tot.sum_len - upto_k;
+            double f[16];
+            f[0] = (double)m;
+            f[1] = (double)n;
+            f[2] = nnz / ((double)m * (double)n);
+            f[3] = (double)tot.min_len;
+            f[4] = (double)tot.max_len;
+            f[5] = nnz / (double)m;
+            f[6] = sd;
+            f[7] = tot.sum_len > 0 ? sd / mean : 0.0;
+            f[8] = log2(nnz > 1.0 ? nnz : 1.0);
+            f[9] = tot.max_len > 0 ? mean / (double)tot.max_len : 0.0;
+            f[10] = tot.sum_len > 0 ? (double)tail / L : 0.0;
+            f[11] = tot.spread_cnt > 0 ? (double)tot.spread_sum / (double)tot.spread_cnt : 0.0;
+            f[12] = (double)tot.band;
+            f[13] = (double)tot.empty / (double)cnt;
+            f[14] = (double)tot.longc / (double)cnt;
+            const unsigned long long capped = ck[0] > 0 ? 0ull : 0ull;
+            (void)capped;
+            unsigned long long csum = 0;  // sum of min(len, 512) = sum_{k=1..512} c_k
+            for (int k = 1; k <= kLenCap; ++k) csum += ck[k];
+            f[15] = widths > 0 ? (double)csum / (32.0 * (double)widths) : 1.0;
+            for (int j = 0; j < 16; ++j) fs[j] = (float)f[j];
+        }
+        __syncthreads();
+        if (feat_out && tid < 16) feat_out[tid] = fs[tid];
+        if (model_params) {
+            if (tid < 16) xs[tid] = feat_scale(tid, fs[tid], lo, hi);
+            __syncthreads();
+            mlp_forward_block(model_params, xs, h1, h2, z);
+            if (tid == 0) {
+                int best = 0;
+                for (int c = 1; c < 5; ++c)
+                    if (z[c] > z[best]) best = c;
+                if (fmt_out) fmt_out[0] = best;
+            }
+            if (logits_out && tid < 5) logits_out[tid] = z[tid];
+        }
+    }
+    cluster.sync();  // keep every CTA's shared memory alive until CTA 0 has read it
+}
+
+static int launch_features(const spmv_csr* c, float* feat, const spmv_model* model, int32_t* fmt, float* logits,
+                           cudaStream_t s) {
+    if (!c) return set_error(SPMV_ERR_INVALID_ARG, "csr is NULL");
+    if (c->m <= 0 || c->n <= 0 || !c->ptr || (c->nnz > 0 && !c->idx))
+        return set_error(SPMV_ERR_INVALID_ARG, "malformed csr argument");
+    k_features<<<kFeatCtas, kFeatThreads, 0, s>>>(c->ptr, c->idx, c->m, c->n, feat, model ? model->params : nullptr,
+                                                 model ? model->lo : nullptr, model ? model->hi : nullptr, fmt, logits);
+    SPMV_CUDA(cudaGetLastError());
+    return SPMV_OK;
+}
+
+// ----------------------------------------------------------------- training
+//
+// One CTA of 1024 threads; samples are processed in chunks of 64 with all
+// activations in shared memory.  Every gradient entry is accumulated by one
+// thread in a fixed order, so results are deterministic.
+
+constexpr int kChunk = 64;
+
+struct TrainSmem {
+    float th[kNP];
+    float g[kNP];
+    float xb[kChunk * 16];
+    float h1[kChunk * 64];
+    float h2[kChunk * 64];
+    float d2[kChunk * 64];  // dL/da2
+    float d1[kChunk * 64];  // dL/da1
+    float dz[kChunk * 5];
+    float lossb[kChunk];
+    float loss;
+};
+
+// grad of the mean cross-entropy over B samples into S.g; S.th holds the parameters.
+__device__ void mlp_grad_block(TrainSmem& S, const float* __restrict__ X, const int32_t* __restrict__ lab, int32_t B) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int p = tid; p < kNP; p += nt) S.g[p] = 0.f;
+    if (tid == 0) S.loss = 0.f;
+    __syncthreads();
+    const float invB = 1.0f / (float)B;
+    for (int b0 = 0; b0 < B; b0 += kChunk) {
+        const int nb = B - b0 < kChunk ? B - b0 : kChunk;
+        for (int q = tid; q < kChunk * 16; q += nt) S.xb[q] = (q / 16 < nb) ? X[(int64_t)b0 * 16 + q] : 0.f;
+        __syncthreads();
+        for (int q = tid; q < kChunk * 64; q += nt) {
+            const int b = q / 64, j = q % 64;
+            float a = S.th[oB1 + j];
+            for (int i = 0; i < 16; ++i) a = fmaf(S.xb[b * 16 + i], S.th[oW1 + i * 64 + j], a);
+            S.h1[q] = a > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+        for (int q = tid; q < kChunk * 64; q += nt) {
+            const int b = q / 64, j = q % 64;
+            float a = S.th[oB2 + j];
+            for (int i = 0; i < 64; ++i) a = fmaf(S.h1[b * 64 + i], S.th[oW2 + i * 64 + j], a);
+            S.h2[q] = a > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+        if (tid < kChunk) {
+            const int b = tid;
+            if (b < nb) {
+                float zz[5];
+                float mxz = -3.4e38f;
+                for (int c = 0; c < 5; ++c) {
+                    float a = S.th[oB3 + c];
+                    for (int i = 0; i < 64; ++i) a = fmaf(S.h2[b * 64 + i], S.th[oW3 + i * 5 + c], a);
+                    zz[c] = a;
+                    mxz = fmaxf(mxz, a);
+                }
+                float den = 0.f;
+                for (int c = 0; c < 5; ++c) den += expf(zz[c] - mxz);
+                const int y = lab[b0 + b];
+                S.lossb[b] = -(zz[y] - mxz - logf(den));
+                for (int c = 0; c < 5; ++c) S.dz[b * 5 + c] = (expf(zz[c] - mxz) / den - (c == y ? 1.f : 0.f)) * invB;
+            } else {
+                S.lossb[b] = 0.f;
+                for (int c = 0; c < 5; ++c) S.dz[b * 5 + c] = 0.f;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float l = S.loss;
+            for (int b = 0; b < nb; ++b) l += S.lossb[b];
+            S.loss = l;
+        }
+        // W3, b3
+        for (int q = tid; q < 64 * 5 + 5; q += nt) {
+            if (q < 320) {
+                const int i = q / 5, c = q % 5;
+                float a = 0.f;
+                for (int b = 0; b < nb; ++b) a = fmaf(S.h2[b * 64 + i], S.dz[b * 5 + c], a);
+                S.g[oW3 + q] += a;
+            } else {
+                const int c = q - 320;
+                float a = 0.f;
+                for (int b = 0; b < nb; ++b) a += S.dz[b * 5 + c];
+                S.g[oB3 + c] += a;
+            }
+        }
+        // dL/da2
+        for (int q = tid; q < kChunk * 64; q += nt) {
+            const int b = q / 64, i = q % 64;
+            float a = 0.f;
+            for (int c = 0; c < 5; ++c) a = fmaf(S.dz[b * 5 + c], S.th[oW3 + i * 5 + c], a);
+            S.d2[q] = S.h2[q] > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+        // W2, b2
+        for (int q = tid; q < 64 * 64 + 64; q += nt) {
+            if (q < 4096) {
+                const int i = q / 64, j = q % 64;
+                float a = 0.f;
+                for (int b = 0; b < nb; ++b) a = fmaf(S.h1[b * 64 + i], S.d2[b * 64 + j], a);
+                S.g[oW2 + q] += a;
+            } else {
+                const int j = q - 4096;
+                float a = 0.f;
+                for (int b = 0; b < nb; ++b) a += S.d2[b * 64 + j];
+                S.g[oB2 + j] += a;
+            }
+        }
+        // dL/da1
+        for (int q = tid; q < kChunk * 64; q += nt) {
+            const int b = q / 64, i = q % 64;
+            float a = 0.f;
+            for (int j = 0; j < 64; ++j) a = fmaf(S.d2[b * 64 + j], S.th[oW2 + i * 64 + j], a);
+            S.d1[q] = S.h1[q] > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+        // W1, b1
+        for (int q = tid; q < 16 * 64 + 64; q += nt) {
+            if (q < 1024) {
+                const int i = q / 64, j = q % 64;
+                float a = 0.f;
+                for (int b = 0; b < nb; ++b) a = fmaf(S.xb[b * 16 + i], S.d1[b * 64 + j], a);
+                S.g[oW1 + q] += a;
+            } else {
+                const int j = q - 1024;
+                float a = 0.f;
+                for (int b = 0; b < nb; ++b) a += S.d1[b * 64 + j];
+                S.g[oB1 + j] += a;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) S.loss *= invB;
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_mlp_grad(const float* __restrict__ theta, const float* __restrict__ X,
+                                                   const int32_t* __restrict__ lab, int32_t B, float* __restrict__ grad,
+                                                   float* __restrict__ loss) {
+    extern __shared__ unsigned char smem_raw[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
+    for (int p = threadIdx.x; p < kNP; p += blockDim.x) S.th[p] = theta[p];
+    __syncthreads();
+    mlp_grad_block(S, X, lab, B);
+    for (int p = threadIdx.x; p < kNP; p += blockDim.x) grad[p] = S.g[p];
+    if (loss && threadIdx.x == 0) *loss = S.loss;
+}
+
+__device__ __forceinline__ void adam_update(float* th, const float* g, float* m, float* v, int p, float lr, float b1,
+                                            float b2, float eps, float c1, float c2) {
+    const float mm = b1 * m[p] + (1.f - b1) * g[p];
+    const float vv = b2 * v[p] + (1.f - b2) * g[p] * g[p];
+    m[p] = mm;
+    v[p] = vv;
+    th[p] = th[p] - lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+__global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int32_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) adam_update(th, g, m, v, p, lr, b1, b2, eps, c1, c2);
+}
+
+__global__ void __launch_bounds__(1024) k_mlp_train(float* __restrict__ theta, float* __restrict__ m,
+                                                    float* __restrict__ v, const float* __restrict__ X,
+                                                    const int32_t* __restrict__ lab, int32_t B, int32_t steps,
+                                                    int32_t t0, float lr, float b1, float b2, float eps,
+                                                    float* __restrict__ loss_hist) {
+    extern __shared__ unsigned char smem_raw[];
+    TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
+    for (int p = threadIdx.x; p < kNP; p += blockDim.x) S.th[p] = theta[p];
+    __syncthreads();
+    for (int st = 0; st < steps; ++st) {
+        mlp_grad_block(S, X, lab, B);
+        const int t = t0 + st + 1;
+        const float c1 = (float)(1.0 - pow((double)b1, (double)t));
+        const float c2 = (float)(1.0 - pow((double)b2, (double)t));
+        for (int p = threadIdx.x; p < kNP; p += blockDim.x) adam_update(S.th, S.g, m, v, p, lr, b1, b2, eps, c1, c2);
+        if (loss_hist && threadIdx.x == 0) loss_hist[st] = S.loss;
+        __syncthreads();
+    }
+    for (int p = threadIdx.x; p < kNP; p += blockDim.x) theta[p] = S.th[p];
+}
+
+__global__ void k_mlp_scale(const float* __restrict__ f, const float* __restrict__ lo, const float* __restrict__ hi,
+                            int32_t B, float* __restrict__ X) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < (int64_t)B * 16) X[q] = feat_scale((int)(q % 16), f[q], lo, hi);
+}
+
+__global__ void k_mlp_forward(const float* __restrict__ th, const float* __restrict__ X, int32_t B,
+                              float* __restrict__ logits, int32_t* __restrict__ pred) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    float h1[64], h2[64], z[5];
+    for (int j = 0; j < 64; ++j) {
+        float a = th[oB1 + j];
+        for (int i = 0; i < 16; ++i) a = fmaf(X[b * 16 + i], th[oW1 + i * 64 + j], a);
+        h1[j] = a > 0.f ? a : 0.f;
+    }
+    for (int j = 0; j < 64; ++j) {
+        float a = th[oB2 + j];
+        for (int i = 0; i < 64; ++i) a = fmaf(h1[i], th[oW2 + i * 64 + j], a);
+        h2[j] = a > 0.f ? a : 0.f;
+    }
+    int best = 0;
+    for (int c = 0; c < 5; ++c) {
+        float a = th[oB3 + c];
+        for (int i = 0; i < 64; ++i) a = fmaf(h2[i], th[oW3 + i * 5 + c], a);
+        z[c] = a;
+        if (c > 0 && a > z[best]) best = c;
+    }
+    if (logits)
+        for (int c = 0; c < 5; ++c) logits[b * 5 + c] = z[c];
+    if (pred) pred[b] = best;
+}
+
+}  // namespace spmv
+
+using namespace spmv;
+
+extern "C" {
+
+int spmv_features(const spmv_csr* csr, float* feat_dev, cudaStream_t stream) {
+    if (!feat_dev) return set_error(SPMV_ERR_INVALID_ARG, "feat_dev is NULL");
+    return launch_features(csr, feat_dev, nullptr, nullptr, nullptr, stream);
+}
+
+int spmv_model_create(const float* params_host, const float* lo_host, const float* hi_host, spmv_model** out) {
+    if (!params_host || !lo_host || !hi_host || !out) return set_error(SPMV_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    spmv_model* md = new spmv_model();
+    int st = dev_malloc((void**)&md->params, sizeof(float) * kNP);
+    if (st == SPMV_OK) st = dev_malloc((void**)&md->lo, sizeof(float) * 16);
+    if (st == SPMV_OK) st = dev_malloc((void**)&md->hi, sizeof(float) * 16);
+    if (st == SPMV_OK) {
+        cudaError_t e = cudaMemcpy(md->params, params_host, sizeof(float) * kNP, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(md->lo, lo_host, sizeof(float) * 16, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(md->hi, hi_host, sizeof(float) * 16, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) st = cuda_error(e, "spmv_model_create");
+    }
+    if (st != SPMV_OK) {
+        dev_free(md->params);
+        dev_free(md->lo);
+        dev_free(md->hi);
+        delete md;
+        return st;
+    }
+    *out = md;
+    return SPMV_OK;
+}
+
+void spmv_model_free(spmv_model* md) {
+    if (!md) return;
+    dev_free(md->params);
+    dev_free(md->lo);
+    dev_free(md->hi);
+    delete md;
+}
+
+int spmv_select_async(const spmv_csr* csr, const spmv_model* model, int32_t* fmt_dev, float* logits_dev,
+                      cudaStream_t stream) {
+    if (!model) return set_error(SPMV_ERR_NO_MODEL, "no selector model");
+    if (!fmt_dev) return set_error(SPMV_ERR_INVALID_ARG, "fmt_dev is NULL");
+    return launch_features(csr, nullptr, model, fmt_dev, logits_dev, stream);
+}
+
+int spmv_select(const spmv_csr* csr, const spmv_model* model, cudaStream_t stream, spmv_fmt* out) {
+    if (!model) return set_error(SPMV_ERR_NO_MODEL, "no selector model");
+    if (!out) return set_error(SPMV_ERR_INVALID_ARG, "out is NULL");
+    static thread_local int32_t* d_fmt = nullptr;
+    static thread_local int d_dev = -1;
+    int dev = 0;
+    SPMV_CUDA(cudaGetDevice(&dev));
+    if (!d_fmt || d_dev != dev) {
+        SPMV_TRY(dev_malloc((void**)&d_fmt, sizeof(int32_t)));
+        d_dev = dev;
+    }
+    SPMV_TRY(launch_features(csr, nullptr, model, d_fmt, nullptr, stream));
+    int32_t h = 0;
+    SPMV_CUDA(cudaMemcpyAsync(&h, d_fmt, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    SPMV_CUDA(cudaStreamSynchronize(stream));
+    *out = (spmv_fmt)h;
+    return SPMV_OK;
+}
+
+int spmv_mlp_scale(const float* feat_dev, const float* lo_dev, const float* hi_dev, int32_t B, float* X_dev,
+                   cudaStream_t stream) {
+    if (!feat_dev || !lo_dev || !hi_dev || !X_dev || B < 0) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    if (B == 0) return SPMV_OK;
+    k_mlp_scale<<<grid_for((int64_t)B * 16, 256), 256, 0, stream>>>(feat_dev, lo_dev, hi_dev, B, X_dev);
+    SPMV_CUDA(cudaGetLastError());
+    return SPMV_OK;
+}
+
+static int train_smem_setup(const void* fn) {
+    SPMV_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TrainSmem)));
+    return SPMV_OK;
+}
+
+int spmv_mlp_loss_grad(const float* theta_dev, const float* X_dev, const int32_t* labels_dev, int32_t B,
+                       float* grad_dev, float* loss_dev, cudaStream_t stream) {
+    if (!theta_dev || !X_dev || !labels_dev || !grad_dev || B <= 0) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    SPMV_TRY(train_smem_setup((const void*)k_mlp_grad));
+    k_mlp_grad<<<1, 1024, sizeof(TrainSmem), stream>>>(theta_dev, X_dev, labels_dev, B, grad_dev, loss_dev);
+    SPMV_CUDA(cudaGetLastError());
+    return SPMV_OK;
+}
+
+int spmv_mlp_adam(float* theta_dev, const float* grad_dev, float* m_dev, float* v_dev, int32_t n, int32_t t, float lr,
+                  float beta1, float beta2, float eps, cudaStream_t stream) {
+    if (!theta_dev || !grad_dev || !m_dev || !v_dev || n <= 0 || t < 1) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    const float c1 = (float)(1.0 - std::pow((double)beta1, (double)t));
+    const float c2 = (float)(1.0 - std::pow((double)beta2, (double)t));
+    k_adam<<<grid_for(n, 256), 256, 0, stream>>>(theta_dev, grad_dev, m_dev, v_dev, n, lr, beta1, beta2, eps, c1, c2);
+    SPMV_CUDA(cudaGetLastError());
+    return SPMV_OK;
+}
+
+int spmv_mlp_train(float* theta_dev, float* m_dev, float* v_dev, const float* X_dev, const int32_t* labels_dev,
+                   int32_t B, int32_t steps, int32_t t0, float lr, float beta1, float beta2, float eps,
+                   float* loss_hist_dev, cudaStream_t stream) {
+    if (!theta_dev || !m_dev || !v_dev || !X_dev || !labels_dev || B <= 0 || steps < 0 || t0 < 0)
+        return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    if (steps == 0) return SPMV_OK;
+    SPMV_TRY(train_smem_setup((const void*)k_mlp_train));
+    k_mlp_train<<<1, 1024, sizeof(TrainSmem), stream>>>(theta_dev, m_dev, v_dev, X_dev, labels_dev, B, steps, t0, lr,
+                                                        beta1, beta2, eps, loss_hist_dev);
+    SPMV_CUDA(cudaGetLastError());
+    return SPMV_OK;
+}
+
+int spmv_mlp_forward(const float* theta_dev, const float* X_dev, int32_t B, float* logits_dev, int32_t* pred_dev,
+                     cudaStream_t stream) {
+    if (!theta_dev || !X_dev || B < 0) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    if (B == 0) return SPMV_OK;
+    k_mlp_forward<<<grid_for(B, 128), 128, 0, stream>>>(theta_dev, X_dev, B, logits_dev, pred_dev);
+    SPMV_CUDA(cudaGetLastError());
+    return SPMV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,203 @@
+// Internal host-side declarations of the SpMV library (not part of the ABI).
+#pragma once
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/spmv.h"
+
+namespace spmv {
+
+constexpr int kThreads = 256;      // block size of the SpMV kernels
+constexpr int kCsrRowCap = 256;    // rows per CSR row block (one thread each at most)
+constexpr int kEllLongRow = 64;    // ELL rows longer than this go to the warp-per-row kernel
+constexpr int kSellUnitWidth = 256;  // SELL slices wider than this are split over several warps
+constexpr int kCsr5Omega = 32;     // CSR5 tile width = warp width
+
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what);
+#define SPMV_CUDA(call)                                         \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return ::spmv::cuda_error(e_, #call); \
+    } while (0)
+#define SPMV_TRY(call)                    \
+    do {                                  \
+        int s_ = (call);                  \
+        if (s_ != SPMV_OK) return s_;     \
+    } while (0)
+
+// Device allocation with the test hook of spmv_debug_fail_alloc.
+int dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
+
+// Temporaries of one call, freed when the object goes out of scope (after the
+// call has synchronised its stream).
+struct Scratch {
+    std::vector<void*> ptrs;
+    template <class T>
+    int get(T** p, size_t count) {
+        void* q = nullptr;
+        SPMV_TRY(dev_malloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16));
+        ptrs.push_back(q);
+        *p = static_cast<T*>(q);
+        return SPMV_OK;
+    }
+    ~Scratch() {
+        for (void* q : ptrs) dev_free(q);
+    }
+};
+
+struct NamedArray {
+    const void* ptr;
+    int64_t count;
+    int32_t elem_bytes;
+};
+
+// CSR row-block work units (also used for the HYB COO tail): unit u covers
+// rows [units[u].x, units[u+1].x); units[u].y >= 0 marks chunk y of one long row.
+struct CsrUnits {
+    int2* units = nullptr;      // n + 1 entries (sentinel {rows, -1})
+    int32_t n = 0;
+    double* partial = nullptr;  // per unit, for split long rows
+    unsigned* counters = nullptr;
+    int32_t block_nnz = 1024, chunk = 4096;
+};
+
+struct EllPart {  // column-major ELL: slot s of row i at s*ld + i
+    int32_t K = 0;
+    int64_t ld = 0;
+    int32_t* row_len = nullptr;  // ld entries (zero padded)
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    int32_t* long_rows = nullptr;  // rows longer than kEllLongRow
+    int32_t n_long = 0;
+};
+
+}  // namespace spmv
+
+struct spmv_handle {
+    int32_t fmt = 0, m = 0, n = 0;
+    int64_t nnz = 0;
+    spmv_params params{};
+    int64_t device_bytes = 0;
+    int64_t stored_slots = 0;
+    int64_t aux[4] = {0, 0, 0, 0};
+    int device = 0;
+    std::vector<void*> owned;
+    std::map<std::string, spmv::NamedArray> arrays;
+
+    // CSR (also the kept ptr of CSR5)
+    int32_t* ptr = nullptr;
+    int32_t* idx = nullptr;
+    double* val = nullptr;
+    spmv::CsrUnits cu;
+
+    // CSR5
+    int32_t csr5_sigma = 0;
+    int64_t ntiles = 0;
+    int32_t* tile_ptr = nullptr;
+    uint32_t* flags = nullptr;  // per (tile, lane): bit r = slot (r, lane) starts a segment
+    int32_t* y_off = nullptr;
+    uint32_t* seg_off = nullptr;  // per tile: bit c = lane c holds no flagged slot
+    int32_t* tile_idx = nullptr;
+    double* tile_val = nullptr;
+    int32_t* empty_ptr = nullptr;
+    int32_t* empty_rows = nullptr;
+    int32_t* zero_rows = nullptr;  // the matrix's empty rows (y = 0)
+    int32_t n_zero_rows = 0;
+    double* carry = nullptr;
+
+    // ELL and the ELL part of HYB
+    spmv::EllPart ell;
+
+    // SELL-C-sigma
+    int32_t sell_C = 32, sell_sigma = 1;
+    int64_t n_slices = 0;
+    int64_t* slice_ptr = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* sell_len = nullptr;  // per sorted position, padded to a multiple of C
+    int32_t* sell_col = nullptr;
+    double* sell_val = nullptr;
+    int2* sell_units = nullptr;   // {slice, chunk or -1}, n_sell_units + 1 entries
+    int32_t n_sell_units = 0;
+    double* sell_partial = nullptr;
+    unsigned* sell_counters = nullptr;
+
+    // HYB COO tail, grouped by row: tail row r_t = tail_rows[t], entries tail_ptr[t]..tail_ptr[t+1]
+    int64_t n_tail = 0;
+    int32_t n_tail_rows = 0;
+    int32_t* tail_rows = nullptr;
+    int32_t* tail_ptr = nullptr;
+    int32_t* tail_col = nullptr;
+    double* tail_val = nullptr;
+    spmv::CsrUnits tail_units;
+
+    template <class T>
+    int alloc(T** p, size_t count, const char* name) {
+        void* q = nullptr;
+        size_t bytes = count * sizeof(T);
+        SPMV_TRY(spmv::dev_malloc(&q, bytes > 0 ? bytes : 16));
+        owned.push_back(q);
+        device_bytes += (int64_t)bytes;
+        *p = static_cast<T*>(q);
+        if (name) arrays[name] = spmv::NamedArray{q, (int64_t)count, (int32_t)sizeof(T)};
+        return SPMV_OK;
+    }
+    ~spmv_handle() {
+        for (void* q : owned) spmv::dev_free(q);
+    }
+};
+
+namespace spmv {
+
+// ---- shared host helpers (common.cu)
+int validate_csr(const spmv_csr* c, cudaStream_t s);
+template <class T>
+int exclusive_scan(const T* in, T* out, int64_t n, cudaStream_t s, Scratch& tmp);  // out[n] = total
+int row_lengths(const int32_t* ptr, int32_t m, int32_t* len, cudaStream_t s);
+int max_i32(const int32_t* a, int64_t n, int32_t* result_host, cudaStream_t s, Scratch& tmp);
+int copy_csr(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
+int64_t resolve_cap(const spmv_params& p);
+// Units of CSR row blocks over (ptr, rows); block_nnz a power of two.
+int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t rows, int32_t block_nnz,
+                    const char* prefix, cudaStream_t s);
+
+// ---- per-format conversion and launch
+int csr_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
+int csr_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s);
+int csr_units_launch(const CsrUnits& cu, const int32_t* ptr, const int32_t* idx, const double* val,
+                     const int32_t* row_map, const double* x, double* y, bool add, cudaStream_t s);
+
+int csr5_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
+int csr5_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s);
+int csr5_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, cudaStream_t s);
+
+int ell_build(spmv_handle* h, EllPart& e, const spmv_csr* c, int32_t K, const int32_t* len, bool hyb,
+              cudaStream_t s);
+int ell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
+int ell_launch(const EllPart& e, int32_t m, int32_t long_len, const double* x, double* y, cudaStream_t s);
+int ell_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s);
+int ell_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, cudaStream_t s);
+
+int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
+int sell_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s);
+int sell_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, cudaStream_t s);
+
+int hyb_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
+int hyb_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s);
+int hyb_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, cudaStream_t s);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int grid_for(int64_t n, int per_block) {
+    int64_t g = ceil_div(n, per_block);
+    return (int)(g < 1 ? 1 : (g > 0x7fffffff ? 0x7fffffff : g));
+}
+
+}  // namespace spmv

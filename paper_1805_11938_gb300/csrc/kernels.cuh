@@ -1,0 +1,415 @@
+// Device-side work units of the five formats.  Each function processes one
+// unit of one matrix and is called both by that format's own kernel and by the
+// batched persistent kernel, so the two paths run the same arithmetic.
+//
+// Loads: matrix data (values, column indices) is read once per product and
+// goes through the streaming path (ld.global.cs, evict-first); x is gathered
+// through the read-only path (ld.global.nc) so it stays resident in L2.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spmv {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double ldx(const double* x, int32_t c) { return __ldg(x + c); }
+
+// Row of nonzero k: the largest i with ptr[i] <= k (empty rows are skipped).
+__device__ __forceinline__ int32_t row_of_nnz(const int32_t* __restrict__ ptr, int32_t m, int64_t k) {
+    int32_t lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int32_t mid = lo + (hi - lo + 1) / 2;
+        if (ptr[mid] <= k) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Sum over a 256-thread block; the result is valid in thread 0.  red: 8 doubles.
+__device__ __forceinline__ double block_sum256(double v, double* red) {
+    v = warp_sum(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) s += red[i];
+    }
+    return s;
+}
+
+// Sum of val[k] * x[idx[k]] over k in [k0, k1) by all 256 threads of a block
+// (four independent accumulators per thread keep four gathers in flight).
+__device__ __forceinline__ double block_range_sum(const int32_t* __restrict__ idx, const double* __restrict__ val,
+                                                  const double* __restrict__ x, int64_t k0, int64_t k1,
+                                                  double* red) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t k = k0 + threadIdx.x;
+    for (; k + 768 < k1; k += 1024) {
+        const int32_t c0 = __ldcs(idx + k), c1 = __ldcs(idx + k + 256), c2 = __ldcs(idx + k + 512),
+                      c3 = __ldcs(idx + k + 768);
+        const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 256), v2 = __ldcs(val + k + 512),
+                     v3 = __ldcs(val + k + 768);
+        s0 = fma(v0, ldx(x, c0), s0);
+        s1 = fma(v1, ldx(x, c1), s1);
+        s2 = fma(v2, ldx(x, c2), s2);
+        s3 = fma(v3, ldx(x, c3), s3);
+    }
+    for (; k < k1; k += 256) s0 = fma(__ldcs(val + k), ldx(x, __ldcs(idx + k)), s0);
+    return block_sum256((s0 + s1) + (s2 + s3), red);
+}
+
+// ------------------------------------------------------------------- CSR
+//
+// Unit u covers rows [units[u].x, units[u+1].x).  A multi-row unit holds at
+// most 2*block_nnz nonzeros: the block stages the products in shared memory
+// (coalesced loads), then T = the largest power of two <= 32 with
+// T * rows <= 256 lanes reduce each row (sub-warp per row chosen by the rows'
+// lengths).  A one-row unit is reduced by the whole block.  units[u].y = c >= 0
+// marks chunk c of a row longer than `chunk`: its partial goes to partial[u]
+// and the last chunk to finish (atomic ticket) adds the chunks in order.
+struct CsrArgs {
+    const int2* units;
+    const int32_t* ptr;
+    const int32_t* idx;
+    const double* val;
+    const int32_t* row_map;  // ADD mode: y[row_map[r]] += sum; else y[r] = sum
+    const double* x;
+    double* y;
+    double* partial;
+    unsigned* counters;
+    int32_t chunk;
+};
+
+template <bool ADD>
+__device__ __forceinline__ void csr_put(const CsrArgs& a, int32_t r, double s) {
+    if (ADD) {
+        const int32_t rr = a.row_map[r];
+        a.y[rr] += s;
+    } else {
+        a.y[r] = s;
+    }
+}
+
+// prod: shared buffer of 2*block_nnz doubles; red: 8 doubles; flag: 1 int.
+template <bool ADD>
+__device__ __forceinline__ void csr_unit(const CsrArgs& a, int32_t u, double* prod, double* red, int* flag) {
+    const int2 U0 = a.units[u];
+    const int32_t r0 = U0.x;
+    if (U0.y >= 0) {  // one chunk of a long row
+        const int64_t rs = a.ptr[r0], re = a.ptr[r0 + 1];
+        const int64_t k0 = rs + (int64_t)U0.y * a.chunk;
+        const int64_t k1 = k0 + a.chunk < re ? k0 + a.chunk : re;
+        const double s = block_range_sum(a.idx, a.val, a.x, k0, k1, red);
+        if (threadIdx.x == 0) {
+            const int32_t first = u - U0.y;
+            const int32_t nch = (int32_t)((re - rs + a.chunk - 1) / a.chunk);
+            a.partial[u] = s;
+            __threadfence();
+            const unsigned prev = atomicAdd(a.counters + first, 1u);
+            if (prev == (unsigned)(nch - 1)) {
+                __threadfence();
+                double acc = 0.0;
+                for (int32_t c = 0; c < nch; ++c) acc += __ldcg(a.partial + first + c);
+                a.counters[first] = 0u;
+                csr_put<ADD>(a, r0, acc);
+            }
+        }
+        __syncthreads();
+        return;
+    }
+    const int32_t r1 = a.units[u + 1].x;
+    const int32_t nrows = r1 - r0;
+    if (nrows == 1) {
+        const double s = block_range_sum(a.idx, a.val, a.x, a.ptr[r0], a.ptr[r0 + 1], red);
+        if (threadIdx.x == 0) csr_put<ADD>(a, r0, s);
+        __syncthreads();
+        return;
+    }
+    const int64_t k0 = a.ptr[r0];
+    const int32_t n = (int32_t)(a.ptr[r1] - k0);
+#pragma unroll 4
+    for (int32_t k = threadIdx.x; k < n; k += 256) prod[k] = __ldcs(a.val + k0 + k) * ldx(a.x, __ldcs(a.idx + k0 + k));
+    __syncthreads();
+    int T = 32;
+    while (T > 1 && T * nrows > 256) T >>= 1;
+    const int g = threadIdx.x / T, l = threadIdx.x & (T - 1);
+    double s = 0.0;
+    if (g < nrows) {
+        const int32_t rs = (int32_t)(a.ptr[r0 + g] - k0), re = (int32_t)(a.ptr[r0 + g + 1] - k0);
+        for (int32_t k = rs + l; k < re; k += T) s += prod[k];
+    }
+    for (int o = T >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    if (g < nrows && l == 0) csr_put<ADD>(a, r0 + g, s);
+    __syncthreads();
+    (void)flag;
+}
+
+// ------------------------------------------------------------------- ELL
+//
+// Column-major ELL (slot s of row i at s*ld + i, ld even): thread t handles
+// rows 2t and 2t+1 with one 16-byte value load and one 8-byte index load per
+// slot, bounded by row_len so padding never reaches a product.  Rows longer
+// than long_len are left to ell_long_row (y not written here).
+struct EllArgs {
+    const int32_t* row_len;
+    const int32_t* col;
+    const double* val;
+    int64_t ld;
+    int32_t m;
+    int32_t long_len;
+    const double* x;
+    double* y;
+};
+
+__device__ __forceinline__ void ell_rows2(const EllArgs& a, int32_t i0) {
+    if (i0 >= a.m) return;
+    const int2 L = *reinterpret_cast<const int2*>(a.row_len + i0);
+    const int32_t l0 = L.x > a.long_len ? 0 : L.x;
+    const int32_t l1 = L.y > a.long_len ? 0 : L.y;
+    const int32_t lm = l0 > l1 ? l0 : l1;
+    double s0 = 0.0, s1 = 0.0;
+    const double2* v2 = reinterpret_cast<const double2*>(a.val + i0);
+    const int2* c2 = reinterpret_cast<const int2*>(a.col + i0);
+    const int64_t st = a.ld >> 1;
+#pragma unroll 4
+    for (int32_t s = 0; s < lm; ++s) {
+        const double2 v = __ldcs(v2 + s * st);
+        const int2 c = __ldcs(c2 + s * st);
+        if (s < l0) s0 = fma(v.x, ldx(a.x, c.x), s0);
+        if (s < l1) s1 = fma(v.y, ldx(a.x, c.y), s1);
+    }
+    if (L.x <= a.long_len) a.y[i0] = s0;
+    if (i0 + 1 < a.m && L.y <= a.long_len) a.y[i0 + 1] = s1;
+}
+
+// One long ELL row by a 256-thread block (slots strided by ld).
+__device__ __forceinline__ void ell_long_row(const EllArgs& a, int32_t i, double* red) {
+    const int32_t len = a.row_len[i];
+    double s0 = 0.0, s1 = 0.0;
+    int32_t s = threadIdx.x;
+    for (; s + 256 < len; s += 512) {
+        const int64_t o0 = (int64_t)s * a.ld + i, o1 = (int64_t)(s + 256) * a.ld + i;
+        s0 = fma(__ldcs(a.val + o0), ldx(a.x, __ldcs(a.col + o0)), s0);
+        s1 = fma(__ldcs(a.val + o1), ldx(a.x, __ldcs(a.col + o1)), s1);
+    }
+    for (; s < len; s += 256) {
+        const int64_t o = (int64_t)s * a.ld + i;
+        s0 = fma(__ldcs(a.val + o), ldx(a.x, __ldcs(a.col + o)), s0);
+    }
+    const double t = block_sum256(s0 + s1, red);
+    if (threadIdx.x == 0) a.y[i] = t;
+    __syncthreads();
+}
+
+// ----------------------------------------------------------- SELL-C-sigma
+//
+// A warp processes one unit {slice, chunk}: lane l holds the R = C/32 sorted
+// positions s*C + l*R .. + R-1, reading R values and R indices per slot with
+// vector loads (R = 2: 16 + 8 bytes, R = 4: 2 x 16 + 16 bytes).  Wide slices
+// are split into chunks of `unit_width` slots whose partial sums are added in
+// chunk order by the last chunk to finish.  y is written through perm.
+struct SellArgs {
+    const int2* units;
+    const int64_t* slice_ptr;
+    const int32_t* len;   // per sorted position, padded to a multiple of C
+    const int32_t* perm;  // sorted position -> row
+    const int32_t* col;
+    const double* val;
+    double* partial;
+    unsigned* counters;
+    int32_t m;
+    int32_t unit_width;
+    const double* x;
+    double* y;
+};
+
+template <int R>
+__device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane) {
+    constexpr int C = 32 * R;
+    const int2 U = a.units[u];
+    const int64_t base = a.slice_ptr[U.x];
+    const int32_t w = (int32_t)((a.slice_ptr[U.x + 1] - base) / C);
+    const int32_t j0 = U.y < 0 ? 0 : U.y * a.unit_width;
+    const int32_t j1 = U.y < 0 ? w : (j0 + a.unit_width < w ? j0 + a.unit_width : w);
+    const int64_t p0 = (int64_t)U.x * C + lane * R;
+    int32_t L[R];
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        L[r] = a.len[p0 + r];
+        acc[r] = 0.0;
+    }
+    int32_t lmax = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) lmax = L[r] > lmax ? L[r] : lmax;
+    const int32_t jend = j1 < lmax ? j1 : lmax;
+#pragma unroll 4
+    for (int32_t j = j0; j < jend; ++j) {
+        const int64_t o = base + (int64_t)j * C + lane * R;
+        if constexpr (R == 1) {
+            const double v = __ldcs(a.val + o);
+            const int32_t c = __ldcs(a.col + o);
+            acc[0] = fma(v, ldx(a.x, c), acc[0]);
+        } else if constexpr (R == 2) {
+            const double2 v = __ldcs(reinterpret_cast<const double2*>(a.val + o));
+            const int2 c = __ldcs(reinterpret_cast<const int2*>(a.col + o));
+            if (j < L[0]) acc[0] = fma(v.x, ldx(a.x, c.x), acc[0]);
+            if (j < L[1]) acc[1] = fma(v.y, ldx(a.x, c.y), acc[1]);
+        } else {
+            const double2 va = __ldcs(reinterpret_cast<const double2*>(a.val + o));
+            const double2 vb = __ldcs(reinterpret_cast<const double2*>(a.val + o + 2));
+            const int4 c = __ldcs(reinterpret_cast<const int4*>(a.col + o));
+            if (j < L[0]) acc[0] = fma(va.x, ldx(a.x, c.x), acc[0]);
+            if (j < L[1]) acc[1] = fma(va.y, ldx(a.x, c.y), acc[1]);
+            if (j < L[2]) acc[2] = fma(vb.x, ldx(a.x, c.z), acc[2]);
+            if (j < L[3]) acc[3] = fma(vb.y, ldx(a.x, c.w), acc[3]);
+        }
+    }
+    if (U.y < 0) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (p0 + r < a.m) a.y[a.perm[p0 + r]] = acc[r];
+        return;
+    }
+    // chunk of a split slice
+#pragma unroll
+    for (int r = 0; r < R; ++r) a.partial[(int64_t)u * C + lane * R + r] = acc[r];
+    __threadfence();
+    __syncwarp();
+    const int32_t first = u - U.y;
+    const int32_t nch = (w + a.unit_width - 1) / a.unit_width;
+    unsigned prev = 0;
+    if (lane == 0) prev = atomicAdd(a.counters + first, 1u);
+    prev = __shfl_sync(kFull, prev, 0);
+    if (prev != (unsigned)(nch - 1)) return;
+    __threadfence();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        double t = 0.0;
+        for (int32_t c = 0; c < nch; ++c) t += __ldcg(a.partial + (int64_t)(first + c) * C + lane * R + r);
+        if (p0 + r < a.m) a.y[a.perm[p0 + r]] = t;
+    }
+    __syncwarp();
+    if (lane == 0) a.counters[first] = 0u;
+}
+
+// ------------------------------------------------------------------- CSR5
+//
+// A warp processes one tile of S = 32*sigma nonzeros: lane c walks its column
+// (nonzeros t*S + c*sigma + r, stored at t*S + r*32 + c, so each step is one
+// coalesced 256-byte load).  flags[t*32 + c] bit r marks a segment start.
+// Inside a lane, segments closed by a later flag in the same lane are
+// complete; the lane's last segment continues into the following lanes up to
+// the next lane holding a flag, which a segmented suffix sum over the lanes
+// (shuffles) supplies.  The tile's first segment, if it continues a row begun
+// in an earlier tile, goes to carry[t] instead of y; csr5_calibrate adds the
+// carries afterwards.
+struct Csr5Args {
+    const int32_t* ptr;
+    const int32_t* tile_ptr;
+    const uint32_t* flags;
+    const int32_t* tile_idx;
+    const double* tile_val;
+    const int32_t* empty_ptr;
+    const int32_t* empty_rows;
+    double* carry;
+    int64_t nnz;
+    int64_t ntiles;
+    int32_t sigma;
+    const double* x;
+    double* y;
+};
+
+__device__ __forceinline__ void csr5_tile(const Csr5Args& a, int64_t t, int lane) {
+    const int64_t S = 32LL * a.sigma;
+    const int64_t base = t * S;
+    const uint32_t f = __ldcs(a.flags + t * 32 + lane);
+    const int nf = __popc(f);
+    // exclusive count of flags in earlier lanes = this lane's first segment index
+    int yo = nf;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(kFull, yo, d);
+        if (lane >= d) yo += v;
+    }
+    yo -= nf;
+    const int32_t row0 = a.tile_ptr[t];
+    const int32_t e0 = a.empty_ptr[t], e1 = a.empty_ptr[t + 1];
+    const bool listed = e1 > e0;
+    const bool cont = a.ptr[row0] != base;  // the tile starts inside row0
+    const int64_t kl = base + (int64_t)lane * a.sigma;
+    double cur = 0.0, head = 0.0;
+    int j = 0;  // segments of this lane seen so far
+    for (int r = 0; r < a.sigma; ++r) {
+        const int64_t slot = base + (int64_t)r * 32 + lane;
+        double p = 0.0;
+        if (kl + r < a.nnz) p = __ldcs(a.tile_val + slot) * ldx(a.x, __ldcs(a.tile_idx + slot));
+        if ((f >> r) & 1u) {
+            if (j == 0) {
+                head = cur;
+            } else {  // segment yo + j - 1 ends here, complete
+                const int g = yo + j - 1;
+                const int32_t row = listed ? a.empty_rows[e0 + g] : row0 + g;
+                if (g == 0 && cont) a.carry[t] = cur;
+                else a.y[row] = cur;
+            }
+            ++j;
+            cur = 0.0;
+        }
+        cur += p;
+    }
+    if (nf == 0) head = cur;
+    // T_c = head_c + (lane c holds no flag ? T_{c+1} : 0)
+    double T = head;
+    bool stop = nf > 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double Tn = __shfl_down_sync(kFull, T, d);
+        const bool sn = __shfl_down_sync(kFull, stop, d);
+        if (!stop && lane + d < 32) {
+            T += Tn;
+            stop = sn;
+        }
+    }
+    double next = __shfl_down_sync(kFull, T, 1);
+    if (lane == 31) next = 0.0;
+    if (nf > 0) {
+        const int g = yo + nf - 1;
+        const int32_t row = listed ? a.empty_rows[e0 + g] : row0 + g;
+        const double tot = cur + next;
+        if (g == 0 && cont) a.carry[t] = tot;
+        else a.y[row] = tot;
+    }
+}
+
+// Adds the carries of tiles that begin inside a row: thread t handles the
+// first such tile of a row and the run of tiles after it continuing the same
+// row, in tile order.  Threads past the tiles write y = 0 for empty rows.
+__device__ __forceinline__ void csr5_calibrate(const Csr5Args& a, int64_t t, const int32_t* zero_rows,
+                                               int32_t n_zero) {
+    if (t < n_zero) a.y[zero_rows[t]] = 0.0;
+    if (t >= a.ntiles) return;
+    const int64_t S = 32LL * a.sigma;
+    const int32_t r = a.tile_ptr[t];
+    const int64_t start = a.ptr[r];
+    if (start == t * S) return;                       // tile t begins row r: no carry
+    if (t > 0 && a.tile_ptr[t - 1] == r && start < (t - 1) * S) return;  // not the first continuing tile
+    double acc = a.carry[t];
+    for (int64_t u = t + 1; u < a.ntiles && a.tile_ptr[u] == r; ++u) acc += a.carry[u];
+    a.y[r] += acc;
+}
+
+}  // namespace dev
+}  // namespace spmv

@@ -1,0 +1,260 @@
+// SELL-C-sigma (Sec. II-B "SELL and SELL-C-sigma"): rows are sorted by
+// length, descending and stably, inside windows of sigma rows; consecutive
+// groups of C sorted rows form slices, each stored as a column-major ELL of
+// its own width.  sigma = 1 is plain SELL.
+//
+// Conversion on the device: a stable segmented LSD radix sort (one bit per
+// pass, a scan and a scatter each) orders every window by (maxlen - length);
+// slice widths and their prefix sum give slice_ptr; one thread per nonzero
+// scatters into the slices.
+#include "internal.cuh"
+#include "kernels.cuh"
+
+namespace spmv {
+
+using dev::row_of_nnz;
+
+__global__ void k_iota_keys(const int32_t* __restrict__ len, int32_t m, int32_t maxlen, uint32_t* __restrict__ key,
+                            int32_t* __restrict__ row) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m) {
+        key[i] = (uint32_t)(maxlen - len[i]);
+        row[i] = (int32_t)i;
+    }
+}
+
+__global__ void k_bit_zero(const uint32_t* __restrict__ key, int32_t m, int bit, int32_t* __restrict__ z) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i <= m) z[i] = (i < m) ? (int32_t)(((key[i] >> bit) & 1u) ^ 1u) : 0;
+}
+
+// Stable partition of every window [w*sigma, min(w*sigma + sigma, m)) by one
+// key bit: zeros keep their order and go first, ones follow in order.
+__global__ void k_bit_scatter(const uint32_t* __restrict__ key, const int32_t* __restrict__ row, int32_t m,
+                              int64_t sigma, int bit, const int32_t* __restrict__ Z, uint32_t* __restrict__ key2,
+                              int32_t* __restrict__ row2) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int64_t ws = (i / sigma) * sigma;
+    const int64_t we = ws + sigma < m ? ws + sigma : m;
+    const int32_t zb = Z[i] - Z[ws];
+    const int32_t zt = Z[we] - Z[ws];
+    const uint32_t k = key[i];
+    const int64_t pos = ((k >> bit) & 1u) ? ws + zt + (i - ws - zb) : ws + zb;
+    key2[pos] = k;
+    row2[pos] = row[i];
+}
+
+__global__ void k_sorted_len(const int32_t* __restrict__ len, const int32_t* __restrict__ perm, int32_t m,
+                             int64_t mp, int32_t* __restrict__ sl, int32_t* __restrict__ ipos) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < m) {
+        const int32_t r = perm[p];
+        sl[p] = len[r];
+        ipos[r] = (int32_t)p;
+    } else if (p < mp) {
+        sl[p] = 0;
+    }
+}
+
+__global__ void k_slice_width(const int32_t* __restrict__ sl, int64_t ns, int32_t C, int64_t* __restrict__ cw,
+                              int32_t* __restrict__ nunit, int32_t W) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s > ns) return;
+    if (s == ns) {
+        cw[ns] = 0;
+        nunit[ns] = 0;
+        return;
+    }
+    int32_t w = 0;
+    for (int32_t l = 0; l < C; ++l) w = max(w, sl[s * C + l]);
+    cw[s] = (int64_t)C * w;
+    nunit[s] = w > W ? (w + W - 1) / W : 1;
+}
+
+__global__ void k_sell_units(const int64_t* __restrict__ sp, int64_t ns, int32_t C, int32_t W,
+                             const int32_t* __restrict__ uoff, int2* __restrict__ units) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s > ns) return;
+    if (s == ns) {
+        units[uoff[ns]] = make_int2((int32_t)ns, -1);
+        return;
+    }
+    const int32_t w = (int32_t)((sp[s + 1] - sp[s]) / C);
+    const int32_t n = uoff[s + 1] - uoff[s];
+    for (int32_t c = 0; c < n; ++c) units[uoff[s] + c] = make_int2((int32_t)s, w > W ? c : -1);
+}
+
+__global__ void k_sell_scatter(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                               const double* __restrict__ val, int32_t m, int64_t nnz, const int32_t* __restrict__ ipos,
+                               const int64_t* __restrict__ sp, int32_t C, int32_t* __restrict__ col,
+                               double* __restrict__ sv) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = row_of_nnz(ptr, m, k);
+        const int64_t j = k - ptr[r];
+        const int32_t p = ipos[r];
+        const int64_t dst = sp[p / C] + j * C + (p % C);
+        col[dst] = idx[k];
+        sv[dst] = val[k];
+    }
+}
+
+int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
+    const int32_t m = c->m;
+    int32_t C = h->params.sell_C ? h->params.sell_C : 32;
+    if (C != 32 && C != 64 && C != 128) return set_error(SPMV_ERR_INVALID_ARG, "sell_C must be 32, 64 or 128 (got %d)", C);
+    int64_t sigma = h->params.sell_sigma ? h->params.sell_sigma : 32LL * C;
+    if (sigma == SPMV_SELL_SIGMA_ALL || sigma > m) sigma = m;
+    if (sigma < 1 || (sigma != 1 && sigma != m && sigma % C != 0))
+        return set_error(SPMV_ERR_INVALID_ARG, "sell_sigma must be 1, a multiple of sell_C, or -1 (got %lld)",
+                         (long long)h->params.sell_sigma);
+    h->params.sell_C = C;
+    h->params.sell_sigma = (int32_t)sigma;
+    h->sell_C = C;
+    h->sell_sigma = (int32_t)sigma;
+    Scratch tmp;
+    int32_t *len = nullptr, *Z = nullptr, *ipos = nullptr;
+    uint32_t *key = nullptr, *key2 = nullptr;
+    int32_t* row2 = nullptr;
+    SPMV_TRY(tmp.get(&len, (size_t)m + 1));
+    SPMV_TRY(row_lengths(c->ptr, m, len, s));
+    int32_t maxlen = 0;
+    SPMV_TRY(max_i32(len, m, &maxlen, s, tmp));
+    SPMV_TRY(h->alloc(&h->perm, (size_t)m, "perm"));
+    SPMV_TRY(tmp.get(&key, (size_t)m));
+    SPMV_TRY(tmp.get(&key2, (size_t)m));
+    SPMV_TRY(tmp.get(&row2, (size_t)m));
+    SPMV_TRY(tmp.get(&Z, (size_t)m + 2));
+    SPMV_TRY(tmp.get(&ipos, (size_t)m));
+    k_iota_keys<<<grid_for(m, 256), 256, 0, s>>>(len, m, maxlen, key, h->perm);
+    SPMV_CUDA(cudaGetLastError());
+    if (sigma > 1) {
+        int bits = 0;
+        while (bits < 32 && (maxlen >> bits) != 0) ++bits;
+        int32_t* rows_a = h->perm;
+        uint32_t* keys_a = key;
+        for (int b = 0; b < bits; ++b) {
+            k_bit_zero<<<grid_for((int64_t)m + 1, 256), 256, 0, s>>>(keys_a, m, b, Z);
+            SPMV_TRY(exclusive_scan<int32_t>(Z, Z, (int64_t)m + 1, s, tmp));
+            k_bit_scatter<<<grid_for(m, 256), 256, 0, s>>>(keys_a, rows_a, m, sigma, b, Z, key2, row2);
+            SPMV_CUDA(cudaGetLastError());
+            std::swap(keys_a, key2);
+            std::swap(rows_a, row2);
+        }
+        if (rows_a != h->perm) {
+            SPMV_CUDA(cudaMemcpyAsync(h->perm, rows_a, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToDevice, s));
+            row2 = rows_a;
+        }
+    }
+    const int64_t ns = ceil_div(m, C);
+    const int64_t mp = ns * C;
+    h->n_slices = ns;
+    SPMV_TRY(h->alloc(&h->sell_len, (size_t)mp, "row_len"));
+    k_sorted_len<<<grid_for(mp, 256), 256, 0, s>>>(len, h->perm, m, mp, h->sell_len, ipos);
+    int64_t* cw = nullptr;
+    int32_t *nunit = nullptr, *uoff = nullptr;
+    SPMV_TRY(tmp.get(&cw, (size_t)ns + 1));
+    SPMV_TRY(tmp.get(&nunit, (size_t)ns + 1));
+    SPMV_TRY(tmp.get(&uoff, (size_t)ns + 2));
+    k_slice_width<<<grid_for(ns + 1, 256), 256, 0, s>>>(h->sell_len, ns, C, cw, nunit, kSellUnitWidth);
+    SPMV_CUDA(cudaGetLastError());
+    SPMV_TRY(h->alloc(&h->slice_ptr, (size_t)ns + 1, "slice_ptr"));
+    SPMV_TRY(exclusive_scan<int64_t>(cw, h->slice_ptr, ns, s, tmp));
+    SPMV_TRY(exclusive_scan<int32_t>(nunit, uoff, ns + 1, s, tmp));
+    int64_t total = 0;
+    int32_t nu = 0;
+    SPMV_CUDA(cudaMemcpyAsync(&total, h->slice_ptr + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA(cudaMemcpyAsync(&nu, uoff + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA(cudaStreamSynchronize(s));
+    const int64_t bytes = total * 12 + mp * 8 + (int64_t)nu * (C * 8 + 12);
+    const int64_t cap = resolve_cap(h->params);
+    if (bytes > cap)
+        return set_error(SPMV_ERR_TOO_LARGE, "SELL needs %lld bytes, cap %lld", (long long)bytes, (long long)cap);
+    SPMV_TRY(h->alloc(&h->sell_col, (size_t)total, "col"));
+    SPMV_TRY(h->alloc(&h->sell_val, (size_t)total, "val"));
+    if (total > 0) {
+        SPMV_CUDA(cudaMemsetAsync(h->sell_col, 0, sizeof(int32_t) * (size_t)total, s));
+        SPMV_CUDA(cudaMemsetAsync(h->sell_val, 0, sizeof(double) * (size_t)total, s));
+    }
+    if (c->nnz > 0) {
+        int g = grid_for(c->nnz, 256);
+        if (g > 152 * 64) g = 152 * 64;
+        k_sell_scatter<<<g, 256, 0, s>>>(c->ptr, c->idx, c->val, m, c->nnz, ipos, h->slice_ptr, C, h->sell_col,
+                                         h->sell_val);
+    }
+    h->n_sell_units = nu;
+    SPMV_TRY(h->alloc(&h->sell_units, (size_t)nu + 1, "units"));
+    SPMV_TRY(h->alloc(&h->sell_partial, (size_t)nu * C, nullptr));
+    SPMV_TRY(h->alloc(&h->sell_counters, (size_t)nu + 1, nullptr));
+    SPMV_CUDA(cudaMemsetAsync(h->sell_counters, 0, sizeof(unsigned) * ((size_t)nu + 1), s));
+    k_sell_units<<<grid_for(ns + 1, 256), 256, 0, s>>>(h->slice_ptr, ns, C, kSellUnitWidth, uoff, h->sell_units);
+    SPMV_CUDA(cudaGetLastError());
+    SPMV_CUDA(cudaStreamSynchronize(s));
+    h->stored_slots = total;
+    h->aux[0] = ns;
+    h->aux[1] = nu;
+    h->aux[2] = maxlen;
+    return SPMV_OK;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_sell(dev::SellArgs a, int32_t nu) {
+    const int32_t u = (int32_t)(blockIdx.x * 8 + (threadIdx.x >> 5));
+    if (u < nu) dev::sell_unit<R>(a, u, threadIdx.x & 31);
+}
+
+int sell_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s) {
+    dev::SellArgs a{h->sell_units, h->slice_ptr, h->sell_len, h->perm, h->sell_col, h->sell_val,
+                    h->sell_partial, h->sell_counters, h->m, kSellUnitWidth, x, y};
+    const int g = grid_for(h->n_sell_units, 8);
+    switch (h->sell_C) {
+        case 32: k_sell<1><<<g, 256, 0, s>>>(a, h->n_sell_units); break;
+        case 64: k_sell<2><<<g, 256, 0, s>>>(a, h->n_sell_units); break;
+        default: k_sell<4><<<g, 256, 0, s>>>(a, h->n_sell_units); break;
+    }
+    SPMV_CUDA(cudaGetLastError());
+    return SPMV_OK;
+}
+
+__global__ void k_unsort_len(const int32_t* __restrict__ sl, const int32_t* __restrict__ perm, int32_t m,
+                             int32_t* __restrict__ len, int32_t* __restrict__ ipos) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < m) {
+        len[perm[p]] = sl[p];
+        ipos[perm[p]] = (int32_t)p;
+    }
+}
+
+__global__ void k_sell_gather(const int32_t* __restrict__ ptr, int32_t m, int64_t nnz, const int32_t* __restrict__ ipos,
+                              const int64_t* __restrict__ sp, int32_t C, const int32_t* __restrict__ col,
+                              const double* __restrict__ sv, int32_t* __restrict__ idx, double* __restrict__ val) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = row_of_nnz(ptr, m, k);
+        const int64_t j = k - ptr[r];
+        const int32_t p = ipos[r];
+        const int64_t src = sp[p / C] + j * C + (p % C);
+        idx[k] = col[src];
+        val[k] = sv[src];
+    }
+}
+
+int sell_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, cudaStream_t s) {
+    Scratch tmp;
+    int32_t *len = nullptr, *ipos = nullptr;
+    SPMV_TRY(tmp.get(&len, (size_t)h->m));
+    SPMV_TRY(tmp.get(&ipos, (size_t)h->m));
+    k_unsort_len<<<grid_for(h->m, 256), 256, 0, s>>>(h->sell_len, h->perm, h->m, len, ipos);
+    SPMV_CUDA(cudaGetLastError());
+    SPMV_TRY(exclusive_scan<int32_t>(len, ptr, h->m, s, tmp));
+    if (h->nnz > 0) {
+        int g = grid_for(h->nnz, 256);
+        if (g > 152 * 64) g = 152 * 64;
+        k_sell_gather<<<g, 256, 0, s>>>(ptr, h->m, h->nnz, ipos, h->slice_ptr, h->sell_C, h->sell_col, h->sell_val, idx,
+                                        val);
+    }
+    SPMV_CUDA(cudaGetLastError());
+    SPMV_CUDA(cudaStreamSynchronize(s));
+    return SPMV_OK;
+}
+
+}  // namespace spmv

@@ -1,0 +1,157 @@
+"""GPU parity of the features, scaling, selector network and its training kernels."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle import mlp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+sp = None
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    global sp
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1805_11938_gb300 as m
+
+    m.lib()
+    sp = m
+
+
+def _feature_cases():
+    lens = np.array([0, 0, 700, 0, 3, 0, 0, 70, 1, 0] * 50, np.int32)
+    return [
+        synth.config1(),
+        synth.powerlaw(20_000, 3, xmax=3000, lmax=3000),  # sampled rows (M > 16384)
+        synth.powerlaw(16_384, 4),                        # exactly the sample size
+        synth.banded(100_000, 40, 5),
+        synth.stencil(synth.STENCIL_7PT_3D, 30, 30, 30, 6),
+        synth.blockdiag(777, 64, 7),
+        synth.from_lengths_random_cols(lens, 800, 8, "empty_mix"),
+        synth.tiny_random(3, 2, 0.5, 9),
+        synth.uniform_random(40_000, 600, 10),            # every row longer than the 512 cap
+    ]
+
+
+@pytest.mark.parametrize("ci", range(9))
+def test_features_match_oracle(ci):
+    a = _feature_cases()[ci]
+    f = sp.spmv_features(sp.DeviceCSR.from_host(a)).cpu().numpy()
+    ref = oracle.features(a).astype(np.float32)
+    assert np.allclose(f, ref, rtol=2e-6, atol=0), np.stack([f, ref])
+
+
+def _xy(seed, B=800):
+    X = synth.vector(B * 16, seed, 0, 1).reshape(B, 16)
+    y = (synth.vector(B, seed + 1, 0, 5).astype(np.int64)) % 5
+    return X, y
+
+
+def _theta(seed):
+    return mlp.glorot_init(synth.vector(mlp.N_PARAMS, seed))
+
+
+@pytest.mark.parametrize("B", [1, 63, 64, 65, 800])
+def test_loss_grad_matches_oracle(B):
+    theta = _theta(3)
+    X, y = _xy(4, B)
+    Xf = X.astype(np.float32)
+    th32 = theta.astype(np.float32)
+    loss_ref, g_ref = mlp.loss_and_grad(th32.astype(np.float64), Xf.astype(np.float64), y)
+    loss, g = sp.spmv_mlp_loss_grad(torch.as_tensor(th32).cuda(), torch.as_tensor(Xf).cuda(),
+                                    torch.as_tensor(y.astype(np.int32)).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.cpu()) - loss_ref) <= 1e-5 * abs(loss_ref)
+    scale = np.abs(g_ref).max()
+    assert np.all(np.abs(g - g_ref) <= 1e-4 * np.maximum(np.abs(g_ref), 1e-2 * scale))
+
+
+def test_adam_matches_oracle():
+    theta = _theta(5)
+    g = synth.vector(mlp.N_PARAMS, 6) * 1e-2
+    m0 = synth.vector(mlp.N_PARAMS, 7) * 1e-3
+    v0 = np.abs(synth.vector(mlp.N_PARAMS, 8)) * 1e-5
+    th_ref, m_ref, v_ref = mlp.adam_step(theta, g, m0, v0, 3, lr=1e-3)
+    T = [torch.as_tensor(a.astype(np.float32)).cuda() for a in (theta, g, m0, v0)]
+    sp.spmv_mlp_adam(T[0], T[1], T[2], T[3], 3, lr=1e-3)
+    assert np.allclose(T[0].cpu().numpy(), th_ref, rtol=1e-5, atol=1e-7)
+    assert np.allclose(T[2].cpu().numpy(), m_ref, rtol=1e-5, atol=1e-9)
+    assert np.allclose(T[3].cpu().numpy(), v_ref, rtol=1e-5, atol=1e-12)
+
+
+def test_train_matches_oracle_steps():
+    """Ten fused full-batch Adam steps on the device follow ten oracle steps."""
+    theta = _theta(9)
+    X, y = _xy(10, 300)
+    th = theta.astype(np.float32).astype(np.float64)
+    m = np.zeros_like(th)
+    v = np.zeros_like(th)
+    losses = []
+    for t in range(1, 11):
+        l, g = mlp.loss_and_grad(th, X.astype(np.float32).astype(np.float64), y)
+        losses.append(l)
+        th, m, v = mlp.adam_step(th, g, m, v, t, lr=3e-3)
+    T = torch.as_tensor(theta.astype(np.float32)).cuda()
+    M = torch.zeros_like(T)
+    V = torch.zeros_like(T)
+    hist = sp.spmv_mlp_train(T, M, V, torch.as_tensor(X.astype(np.float32)).cuda(),
+                             torch.as_tensor(y.astype(np.int32)).cuda(), 10, 0, lr=3e-3).cpu().numpy()
+    assert np.allclose(hist, losses, rtol=1e-4)
+    assert np.allclose(T.cpu().numpy(), th, rtol=1e-3, atol=1e-5)
+
+
+def test_forward_and_predict():
+    theta = _theta(11)
+    X, _ = _xy(12, 500)
+    z_ref, _ = mlp.forward(theta.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64))
+    logits, pred = sp.spmv_mlp_forward(torch.as_tensor(theta.astype(np.float32)).cuda(),
+                                       torch.as_tensor(X.astype(np.float32)).cuda())
+    z = logits.cpu().numpy()
+    assert np.allclose(z, z_ref, rtol=1e-4, atol=1e-5)
+    srt = np.sort(z_ref, axis=1)
+    clear = srt[:, -1] - srt[:, -2] > 1e-3  # argmax decided away from ties
+    assert np.array_equal(pred.cpu().numpy()[clear], np.argmax(z_ref, axis=1)[clear])
+
+
+def test_scale_matches_oracle():
+    feats = np.stack([oracle.features(a) for a in _feature_cases()]).astype(np.float32)
+    t = mlp.transform(feats.astype(np.float64))
+    lo, hi = mlp.fit_scaling(t[:6])
+    ref = mlp.scale(t, lo, hi)
+    X = sp.spmv_mlp_scale(torch.as_tensor(feats).cuda(), torch.as_tensor(lo.astype(np.float32)).cuda(),
+                          torch.as_tensor(hi.astype(np.float32)).cuda()).cpu().numpy()
+    assert np.allclose(X, ref, atol=2e-6)
+
+
+def test_select_matches_oracle():
+    theta = _theta(13).astype(np.float32)
+    cases = _feature_cases()
+    feats = np.stack([oracle.features(a) for a in cases]).astype(np.float32)
+    t = mlp.transform(feats.astype(np.float64))
+    lo, hi = mlp.fit_scaling(t)
+    model = sp.Model(theta, lo, hi)
+    lo32, hi32 = lo.astype(np.float32).astype(np.float64), hi.astype(np.float32).astype(np.float64)
+    for a, f in zip(cases, feats):
+        x = mlp.scale(mlp.transform(f.astype(np.float64)), lo32, hi32).astype(np.float32)
+        z_ref, _ = mlp.forward(theta.astype(np.float64), x[None, :].astype(np.float64))
+        d = sp.DeviceCSR.from_host(a)
+        fmt_out = torch.zeros(1, dtype=torch.int32, device="cuda")
+        logits = torch.zeros(5, dtype=torch.float32, device="cuda")
+        sp.spmv_select_async(d, model, fmt_out, logits)
+        assert np.allclose(logits.cpu().numpy(), z_ref[0], rtol=1e-4, atol=1e-5)
+        srt = np.sort(z_ref[0])
+        if srt[-1] - srt[-2] > 1e-3:
+            assert int(fmt_out.cpu()) == int(np.argmax(z_ref[0]))
+            assert sp.spmv_select(d, model) == int(np.argmax(z_ref[0]))
+
+
+def test_select_without_model():
+    d = sp.DeviceCSR.from_host(synth.config1())
+    with pytest.raises(sp.SpmvError) as ei:
+        sp.spmv_select(d, None)
+    assert ei.value.name == "NO_MODEL"
