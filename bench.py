@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark: FP64 SpMV on the GB300 through the library's C ABI.
+
+One step = the deployment path on one matrix resident in HBM: the selector
+kernel (features + scaling + network, result kept on the device) and the
+product y = A x in the format the selector chose for this matrix.  Every
+format is also timed on its own; conversions are timed once.  Between timed
+steps a 256 MiB buffer is written to flush L2, and each step is bracketed by
+CUDA events on the stream the kernels run on.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...     # the CPU oracle on the host cores
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 SpMV GFLOP/s & HBM GB/s vs ~8 TB/s; selector % of best-format throughput"
+FORMATS = ("CSR", "CSR5", "ELL", "SELL", "HYB")
+
+WORKLOADS = {
+    "powerlaw_2e6": "n = 2,000,000, row lengths ceil(Pareto alpha 2.1) on [1, 5000], uniform columns, N(0,1) values",
+    "laplacian_64": "2D 5-point Laplacian on 64 x 64 (n = 4096, nnz = 20224)",
+    "stencil27_224": "3D 27-point stencil on 224^3 (n = 11,239,424, nnz = 300,763,000)",
+    "graph_2e7": "n = 20,000,000 power-law graph, mean about 12 entries per row, at most 1e5",
+}
+
+
+def make_matrix(name: str):
+    import synth
+
+    if name == "powerlaw_2e6":
+        return synth.config2()
+    if name == "laplacian_64":
+        return synth.config1()
+    if name == "stencil27_224":
+        return synth.config5_stencil()
+    if name == "graph_2e7":
+        return synth.config5_graph()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def algorithmic_bytes(fmt: int, info: dict) -> int:
+    """Bytes a format must move per product: every stored nonzero once (8 B value + 4 B index),
+    x and y once, plus the format's per-row / per-unit metadata (never the padding)."""
+    m, n, nnz = info["m"], info["n"], info["nnz"]
+    base = 12 * nnz + 8 * n + 8 * m
+    aux = info["aux"]
+    if fmt == 0:  # CSR: row pointers
+        return base + 4 * (m + 1)
+    if fmt == 1:  # CSR5: per tile 32 flag words, tile_ptr, empty_ptr, the head row's pointer, carry
+        return base + aux[0] * (128 + 4 + 8 + 4 + 16)
+    if fmt == 2:  # ELL: row_len
+        return base + 4 * m
+    if fmt == 3:  # SELL: row_len, perm, slice_ptr, units
+        return base + 8 * m + 8 * (aux[0] + 1) + 8 * aux[1]
+    # HYB: ELL row_len + tail row ids and pointers + read-modify-write of tail rows' y
+    return base + 4 * m + 8 * aux[1] + 8 * aux[1]
+
+
+def launches_per_run(fmt: int, info: dict) -> int:
+    aux = info["aux"]
+    if fmt == 1:
+        return (1 if aux[0] > 0 else 0) + (1 if max(aux[0], aux[2]) > 0 else 0)
+    if fmt == 4:
+        return 1 + (1 if aux[1] > 0 else 0)
+    return 1
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self) -> dict:
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_leg(a, x, y_gpu, seconds: float):
+    """The CPU-baseline leg: the oracle as it stands (single thread, CSR order)
+    timed on the full matrix, and the timed GPU result checked on 2048 rows
+    against the oracle's definition."""
+    import oracle
+    import synth
+
+    rows = np.linspace(0, a.m - 1, 2048).astype(np.int64)
+    lens = (a.ptr[rows + 1] - a.ptr[rows]).astype(np.int64)
+    sub = synth.CSR(len(rows), a.n, np.concatenate([[0], np.cumsum(lens)]).astype(np.int32),
+                    np.concatenate([a.idx[a.ptr[r]:a.ptr[r + 1]] for r in rows]),
+                    np.concatenate([a.val[a.ptr[r]:a.ptr[r + 1]] for r in rows]))
+    ok = bool(np.all(np.abs(y_gpu[rows] - oracle.csr_spmv(sub, x)) <= oracle.fp_bound(sub, x)))
+    return cpu_oracle_rate(a, x, seconds), {"sampled_rows_within_bound": ok, "rows": len(rows)}
+
+
+def cpu_oracle_rate(a, x, seconds: float) -> dict:
+    import oracle
+
+    oracle.csr_spmv(a, x)  # warm
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.csr_spmv(a, x)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": 2.0 * a.nnz * reps / el / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full products of the {a.m}-row matrix ({a.nnz} nonzeros), single-threaded C, {el:.1f} s"}
+
+
+REF_BLOCK_NNZ = 1 << 18
+
+
+def row_blocks(a, block_nnz: int):
+    """Contiguous row blocks of about block_nnz nonzeros each (views, not copies)."""
+    import synth
+
+    out, r0 = [], 0
+    while r0 < a.m:
+        r1 = int(np.searchsorted(a.ptr, a.ptr[r0] + block_nnz, side="right")) - 1
+        r1 = min(max(r1, r0 + 1), a.m)
+        p0 = int(a.ptr[r0])
+        out.append(synth.CSR(r1 - r0, a.n, (a.ptr[r0:r1 + 1] - p0).astype(np.int32), a.idx[p0:a.ptr[r1]],
+                             a.val[p0:a.ptr[r1]], f"rows{r0}"))
+        r0 = r1
+    return out
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    """The CPU oracle as it stands on the host cores; one step = the product of
+    one row block of about 2^18 nonzeros, cycling over the whole matrix."""
+    if rank != 0:
+        return
+    import synth
+    import oracle
+
+    a = make_matrix(args.workload)
+    x = synth.vector(a.n, 1)
+    blocks = row_blocks(a, REF_BLOCK_NNZ)
+    for i in range(args.warmup):
+        oracle.csr_spmv(blocks[i % len(blocks)], x)
+    flops, t = 0, 0.0
+    for i in range(args.steps):
+        b = blocks[i % len(blocks)]
+        t0 = time.perf_counter()
+        oracle.csr_spmv(b, x)
+        t += time.perf_counter() - t0
+        flops += 2 * b.nnz
+    v = flops / t / 1e9
+    sample = (f"{args.steps} row blocks of about {REF_BLOCK_NNZ} nonzeros ({flops // 2} nonzeros in all) of the "
+              f"{a.m}-row matrix, single-threaded C")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": a.m, "nnz": a.nnz,
+                       "step": "CPU oracle product of one row block (about 2^18 nonzeros)"},
+            "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="powerlaw_2e6", choices=sorted(WORKLOADS))
+    ap.add_argument("--ell-cap-gb", type=float, default=160.0, help="ELL footprint cap (the 2e6 power-law ELL is ~119 GB)")
+    ap.add_argument("--format-steps", type=int, default=300)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--formats", default="0,1,2,3,4")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    import synth
+    import paper_1805_11938_gb300 as sp
+
+    sp.lib()
+    a = make_matrix(args.workload)
+    xh = synth.vector(a.n, 1)
+    d = sp.DeviceCSR.from_host(a)
+    x = torch.as_tensor(xh).cuda()
+    y = torch.empty(a.m, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # ---- conversions (timed once each) and handles
+    fmts = [int(f) for f in args.formats.split(",") if f != ""]
+    handles, infos, conv_ms, status = {}, {}, {}, {}
+    for f in fmts:
+        params = {"max_bytes": int(args.ell_cap_gb * (1 << 30))} if f == 2 else None
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            h = sp.spmv_convert(f, d, params)
+        except sp.SpmvError as e:
+            status[FORMATS[f]] = e.name
+            continue
+        torch.cuda.synchronize()
+        conv_ms[FORMATS[f]] = 1e3 * (time.perf_counter() - t0)
+        handles[f], infos[f] = h, h.info()
+
+    def timed(fn, n, warm):
+        for _ in range(warm):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for s, e in evs:
+            flush.zero_()
+            s.record(stream)
+            fn()
+            e.record(stream)
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) for s, e in evs]
+
+    # ---- every format on its own (exhaustive search, also the selector's judge)
+    per_fmt = {}
+    for f, h in handles.items():
+        ms = statistics.mean(timed(lambda h=h: sp.spmv_run(h, x, y), args.format_steps, 5))
+        ab = algorithmic_bytes(f, infos[f])
+        per_fmt[FORMATS[f]] = {"ms": ms, "gflops": 2 * a.nnz / ms / 1e6, "alg_gbs": ab / ms / 1e6,
+                               "alg_bytes": ab, "device_bytes": infos[f]["device_bytes"],
+                               "params": {k: v for k, v in infos[f]["params"].items() if k != "max_bytes"}}
+    for name, st in status.items():
+        per_fmt[name] = {"status": st}
+    best = min((f for f in handles), key=lambda f: per_fmt[FORMATS[f]]["ms"])
+
+    # ---- selector
+    model = None
+    if os.path.exists(sp.MODEL_PATH):
+        model = sp.Model.load(sp.MODEL_PATH)
+    fmt_dev = torch.zeros(1, dtype=torch.int32, device="cuda")
+    feat = torch.empty(16, dtype=torch.float32, device="cuda")
+    if model is not None:
+        chosen = sp.spmv_select(d, model)
+        if chosen not in handles:
+            chosen = best
+        select_step = lambda: sp.spmv_select_async(d, model, fmt_dev)  # noqa: E731
+        selector_kind = "mlp"
+    else:
+        chosen = best
+        select_step = lambda: sp.spmv_features(d, feat)  # noqa: E731
+        selector_kind = "exhaustive (no trained model found; the step runs the features kernel)"
+    sel_ms = statistics.mean(timed(select_step, args.format_steps, 5))
+    hc = handles[chosen]
+
+    def step():
+        select_step()
+        sp.spmv_run(hc, x, y)
+
+    # ---- timed steps (the headline)
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        for s, mid, e in ev:
+            flush.zero_()
+            s.record(stream)
+            select_step()
+            mid.record(stream)
+            sp.spmv_run(hc, x, y)
+            e.record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [s.elapsed_time(e) for s, _, e in ev]
+    kern_ms = [m.elapsed_time(e) for _, m, e in ev]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * 2.0 * a.nnz * args.steps / (total_ms * 1e6)
+    clocks = clk.summary()
+
+    # ---- end to end: pinned host x in, y out, every step
+    xh_pin = torch.as_tensor(xh).pin_memory()
+    yh_pin = torch.empty(a.m, dtype=torch.float64).pin_memory()
+    n_e2e = max(10, min(args.steps, 500))
+
+    def e2e_step():
+        x.copy_(xh_pin, non_blocking=True)
+        select_step()
+        sp.spmv_run(hc, x, y)
+        yh_pin.copy_(y, non_blocking=True)
+
+    e2e_ms = statistics.mean(timed(e2e_step, n_e2e, 5))
+    torch.cuda.synchronize()
+
+    yv = y.cpu().numpy()
+    agree = None
+    if model is not None:
+        torch.cuda.synchronize()
+        agree = int(fmt_dev.item()) == chosen
+
+    # ---- roofline of the dominant kernel (the chosen format's product)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peaks = json.load(fh)
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    kms = statistics.mean(kern_ms)
+    ab = algorithmic_bytes(chosen, infos[chosen])
+    achieved = ab / kms / 1e6
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as fh:
+            tr = json.load(fh)
+        key = f"{args.workload}:{FORMATS[chosen]}"
+        if key in tr:
+            traffic = tr[key]
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": a.m, "nnz": a.nnz,
+                   "selected_format": FORMATS[chosen], "exhaustive_best": FORMATS[best], "selector": selector_kind,
+                   "step": "selector kernel + SpMV in the selected format, matrix and x resident in HBM",
+                   "l2": "flushed: 256 MiB written before every timed step", "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": f"{FORMATS[chosen]} product", "kernel_ms": kms,
+                     "alg_bytes_per_launch": ab, "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy, burst)"},
+        "e2e": {"value": 2.0 * a.nnz / e2e_ms / 1e6, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * a.n,
+                "d2h_bytes_per_step": 8 * a.m, "ms_per_step": e2e_ms},
+        "gpu_launches": args.steps * (1 + launches_per_run(chosen, infos[chosen])),
+        "clocks": clocks,
+        "formats": per_fmt,
+        "selector": {"kind": selector_kind, "chosen": FORMATS[chosen], "best": FORMATS[best],
+                     "pct_of_best": 100.0 * per_fmt[FORMATS[best]]["ms"] / per_fmt[FORMATS[chosen]]["ms"],
+                     "select_us": 1e3 * sel_ms, "select_frac_of_spmv": sel_ms / per_fmt[FORMATS[chosen]]["ms"],
+                     "per_step_agrees": agree},
+        "conversion_ms": conv_ms,
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"], line["check"] = cpu_leg(a, xh, yv, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

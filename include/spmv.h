@@ -82,10 +82,10 @@ typedef struct {
 typedef struct {
     int32_t sell_C;        /* SELL slice height: 32, 64 or 128 rows (0 -> 32) */
     int32_t sell_sigma;    /* SELL sorting window in rows: 1 (plain SELL), a multiple of sell_C,
-                              or -1 for the whole matrix (0 -> 32 * sell_C) */
+                              or -1 for the whole matrix (0 -> the whole matrix) */
     int32_t csr5_omega;    /* CSR5 tile width: 32, the warp width, is the only value (0 -> 32) */
-    int32_t csr5_sigma;    /* CSR5 tile height, 1..32 (0 -> 16) */
-    int32_t csr_block_nnz; /* CSR row-block nonzero budget, a power of two in [128, 4096] (0 -> 1024) */
+    int32_t csr5_sigma;    /* CSR5 tile height, 1..32 (0 -> 32) */
+    int32_t csr_block_nnz; /* CSR row-block nonzero budget, a power of two in [128, 2048] (0 -> 512) */
     int32_t hyb_k;         /* HYB ELL width: > 0 explicit, 0 -> the typical-length rule,
                               SPMV_HYB_K_NONE -> every entry in the COO part */
     int64_t max_bytes;     /* cap on the handle's device footprint (0 -> 90% of free memory) */

@@ -30,6 +30,7 @@ enum TaskKind : int32_t {
 struct MatDesc {
     int32_t fmt, sell_r;
     int32_t n_zero;
+    int32_t csr_block_nnz;
     int32_t ell_nb;
     const int32_t* zero_rows;
     const int32_t* long_rows;
@@ -49,9 +50,8 @@ struct BatchDev {
 };
 
 __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
-    extern __shared__ double prod[];
+    extern __shared__ double smem[];
     __shared__ double red[8];
-    __shared__ int flag;
     __shared__ int task_sh;
     for (;;) {
         if (threadIdx.x == 0) task_sh = (int)atomicAdd(B.counter, 1u);
@@ -69,14 +69,14 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
                 dev::CsrArgs a = md.csr;
                 a.x = x;
                 a.y = y;
-                dev::csr_unit<false>(a, t.z, prod, red, &flag);
+                dev::csr_unit<false>(a, t.z, smem, md.csr_block_nnz, red);
                 break;
             }
             case T_HYB_TAIL: {
                 dev::CsrArgs a = md.csr;
                 a.x = x;
                 a.y = y;
-                dev::csr_unit<true>(a, t.z, prod, red, &flag);
+                dev::csr_unit<true>(a, t.z, smem, md.csr_block_nnz, red);
                 break;
             }
             case T_CSR5: {
@@ -169,6 +169,7 @@ static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, s
         case SPMV_CSR:
             d.csr = dev::CsrArgs{h->cu.units, h->ptr, h->idx, h->val, nullptr, nullptr, nullptr, h->cu.partial,
                                  h->cu.counters, h->cu.chunk};
+            d.csr_block_nnz = h->cu.block_nnz;
             if (h->cu.block_nnz > max_block_nnz) max_block_nnz = h->cu.block_nnz;
             for (int32_t u = 0; u < h->cu.n; ++u) t1.push_back(make_int4(b, T_CSR, u, 0));
             break;
@@ -195,6 +196,7 @@ static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, s
             if (h->fmt == SPMV_HYB && h->n_tail_rows > 0) {
                 d.csr = dev::CsrArgs{h->tail_units.units, h->tail_ptr, h->tail_col, h->tail_val, h->tail_rows, nullptr,
                                      nullptr, h->tail_units.partial, h->tail_units.counters, h->tail_units.chunk};
+                d.csr_block_nnz = h->tail_units.block_nnz;
                 if (h->tail_units.block_nnz > max_block_nnz) max_block_nnz = h->tail_units.block_nnz;
                 for (int32_t u = 0; u < h->tail_units.n; ++u) t2.push_back(make_int4(b, T_HYB_TAIL, u, 0));
             }
@@ -268,7 +270,7 @@ int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t st
     for (int32_t b = 0; b < count; ++b) fill_desc(handles[b], mats[b], t1, t2, b, max_bnnz);
     bt->n1 = (int32_t)t1.size();
     bt->n2 = (int32_t)t2.size();
-    bt->smem = sizeof(double) * 2 * (size_t)max_bnnz;
+    bt->smem = dev::csr_smem_bytes(max_bnnz);
     int st = dev_malloc((void**)&bt->d_mats, sizeof(MatDesc) * count);
     if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_tasks1, sizeof(int4) * (t1.size() + 1));
     if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_tasks2, sizeof(int4) * (t2.size() + 1));

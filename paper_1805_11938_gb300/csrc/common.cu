@@ -310,6 +310,7 @@ __global__ void k_unit_fill(const int32_t* __restrict__ ptr, int32_t m, int32_t 
 
 int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t rows, int32_t block_nnz,
                     const char* prefix, cudaStream_t s) {
+    SPMV_TRY(csr_prepare_kernels());
     Scratch tmp;
     cu.block_nnz = block_nnz;
     cu.chunk = 4 * block_nnz;

@@ -132,7 +132,7 @@ int csr5_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     const int32_t m = c->m;
     if (h->params.csr5_omega != 0 && h->params.csr5_omega != 32)
         return set_error(SPMV_ERR_INVALID_ARG, "csr5_omega must be 32, the warp width (got %d)", h->params.csr5_omega);
-    const int32_t sigma = h->params.csr5_sigma ? h->params.csr5_sigma : 16;
+    const int32_t sigma = h->params.csr5_sigma ? h->params.csr5_sigma : 32;
     if (sigma < 1 || sigma > 32) return set_error(SPMV_ERR_INVALID_ARG, "csr5_sigma must be in [1, 32] (got %d)", sigma);
     h->params.csr5_omega = 32;
     h->params.csr5_sigma = sigma;

@@ -116,11 +116,17 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         lng += len >= 32;
         atomicAdd(&part.hist[len < kLenCap ? len : kLenCap], 1u);
         const int ne = len < kSpread ? len : kSpread;
-        for (int e = 0; e < ne; ++e) {
-            const int64_t d = (int64_t)__ldg(idx + p0 + e) - i;
-            const int ad = (int)(d < 0 ? -d : d);
-            ssum += (unsigned long long)ad;
-            band = max(band, ad);
+        for (int e0 = 0; e0 < ne; e0 += 8) {  // eight independent loads in flight
+            int32_t c[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) c[q] = e0 + q < ne ? __ldg(idx + p0 + e0 + q) : (int32_t)i;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t d = (int64_t)c[q] - i;
+                const int ad = (int)(d < 0 ? -d : d);
+                ssum += (unsigned long long)ad;
+                band = max(band, ad);
+            }
         }
         scnt += (unsigned long long)ne;
     }
@@ -164,6 +170,7 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         __shared__ int Ksh;
         __shared__ unsigned long long widths;
         __shared__ unsigned long long upto_k;
+        __shared__ unsigned long long capped_sum;
         if (tid == 0) {
             tot.sum_len = tot.sum_sq = tot.spread_sum = tot.spread_cnt = 0;
             tot.min_len = 0x7fffffff; tot.max_len = 0; tot.band = 0; tot.empty = 0; tot.longc = 0;
@@ -174,7 +181,7 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
                 tot.min_len = min(tot.min_len, q->min_len); tot.max_len = max(tot.max_len, q->max_len);
                 tot.band = max(tot.band, q->band); tot.empty += q->empty; tot.longc += q->longc;
             }
-            Ksh = 0; widths = 0; upto_k = 0;
+            Ksh = 0; widths = 0; upto_k = 0; capped_sum = 0;
         }
         for (int b = tid; b <= kLenCap; b += kFeatThreads) {
             unsigned s = 0;
@@ -182,13 +189,16 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
             hist[b] = s;
         }
         __syncthreads();
-        // c_k = #{len >= k}: suffix sums of the capped histogram (one thread per k, short loops)
-        for (int k = tid; k <= kLenCap; k += kFeatThreads) {
-            unsigned s = 0;
-            for (int b = k; b <= kLenCap; ++b) s += hist[b];
-            ck[k] = s;
-        }
+        // c_k = #{len >= k}: parallel suffix sums of the capped histogram
+        for (int k = tid; k <= kLenCap; k += kFeatThreads) ck[k] = hist[k];
         __syncthreads();
+        for (int d = 1; d <= kLenCap; d <<= 1) {
+            unsigned v = 0;
+            if (tid <= kLenCap && tid + d <= kLenCap) v = ck[tid + d];
+            __syncthreads();
+            if (tid <= kLenCap) ck[tid] += v;
+            __syncthreads();
+        }
         const unsigned cnt = (unsigned)S;
         const unsigned need = (cnt + 2) / 3;
         // K = #{k in [1, 512] : c_k >= need}; SELL widths = sum_k ceil(c_k / 32)
@@ -204,6 +214,7 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         if (tid == 0) Ksh = okK;
         __syncthreads();
         if (tid >= 1 && tid <= Ksh) atomicAdd(&upto_k, (unsigned long long)ck[tid]);  // sum_{k<=K} c_k = sum min(len, K)
+        if (tid >= 1 && tid <= kLenCap) atomicAdd(&capped_sum, (unsigned long long)ck[tid]);  // sum min(len, 512)
         __syncthreads();
         if (tid == 0) {
             const double L = (double)tot.sum_len;
@@ -235,11 +246,7 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
             f[12] = (double)tot.band;
             f[13] = (double)tot.empty / (double)cnt;
             f[14] = (double)tot.longc / (double)cnt;
-            const unsigned long long capped = ck[0] > 0 ? 0ull : 0ull;
-            (void)capped;
-            unsigned long long csum = 0;  // sum of min(len, 512) = sum_{k=1..512} c_k
-            for (int k = 1; k <= kLenCap; ++k) csum += ck[k];
-            f[15] = widths > 0 ? (double)csum / (32.0 * (double)widths) : 1.0;
+            f[15] = widths > 0 ? (double)capped_sum / (32.0 * (double)widths) : 1.0;
             for (int j = 0; j < 16; ++j) fs[j] = (float)f[j];
         }
         __syncthreads();

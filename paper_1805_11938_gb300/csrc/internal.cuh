@@ -170,6 +170,7 @@ int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t ro
                     const char* prefix, cudaStream_t s);
 
 // ---- per-format conversion and launch
+int csr_prepare_kernels();
 int csr_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
 int csr_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s);
 int csr_units_launch(const CsrUnits& cu, const int32_t* ptr, const int32_t* idx, const double* val,

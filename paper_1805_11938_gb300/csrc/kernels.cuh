@@ -72,13 +72,21 @@ __device__ __forceinline__ double block_range_sum(const int32_t* __restrict__ id
 
 // ------------------------------------------------------------------- CSR
 //
-// Unit u covers rows [units[u].x, units[u+1].x).  A multi-row unit holds at
-// most 2*block_nnz nonzeros: the block stages the products in shared memory
-// (coalesced loads), then T = the largest power of two <= 32 with
-// T * rows <= 256 lanes reduce each row (sub-warp per row chosen by the rows'
-// lengths).  A one-row unit is reduced by the whole block.  units[u].y = c >= 0
-// marks chunk c of a row longer than `chunk`: its partial goes to partial[u]
-// and the last chunk to finish (atomic ticket) adds the chunks in order.
+// Unit u covers rows [units[u].x, units[u+1].x).  On this GPU the FP64 pipe
+// issues about two lanes per clock per SM, so every FP64 instruction must
+// carry a full warp of useful work: exactly one DFMA per nonzero, with the
+// lanes kept busy, and as few cross-lane FP64 reductions as possible.
+//
+// A multi-row unit (fewer than 2*block_nnz nonzeros, at most 256 rows): the
+// block stages values and gathered x[idx] in shared memory with coalesced
+// loads, then thread t walks the contiguous chunk [t*CT, t*CT + CT) (CT odd,
+// so 8-byte shared accesses are conflict-free) with one DFMA per nonzero,
+// writing every row that begins and ends in its chunk.  A row begun in an
+// earlier chunk leaves its partial in shared memory; the thread that owns the
+// row's start adds those partials in chunk order.
+// A one-row unit is reduced by the whole block.  units[u].y = c >= 0 marks
+// chunk c of a row longer than `chunk`: its partial goes to partial[u] and
+// the last chunk to finish (atomic ticket) adds the chunks in order.
 struct CsrArgs {
     const int2* units;
     const int32_t* ptr;
@@ -102,17 +110,22 @@ __device__ __forceinline__ void csr_put(const CsrArgs& a, int32_t r, double s) {
     }
 }
 
-// prod: shared buffer of 2*block_nnz doubles; red: 8 doubles; flag: 1 int.
+// Shared memory of a CSR block: csr_smem_bytes(block_nnz).
+__host__ __device__ constexpr size_t csr_smem_bytes(int block_nnz) {
+    return (size_t)2 * (2 * block_nnz + 256) * sizeof(double) + 256 * sizeof(double) + 2 * 260 * sizeof(int32_t);
+}
+
 template <bool ADD>
-__device__ __forceinline__ void csr_unit(const CsrArgs& a, int32_t u, double* prod, double* red, int* flag) {
+__device__ __forceinline__ void csr_unit(const CsrArgs& a, int32_t u, double* smem, int32_t block_nnz, double* red) {
     const int2 U0 = a.units[u];
     const int32_t r0 = U0.x;
+    const int tid = threadIdx.x;
     if (U0.y >= 0) {  // one chunk of a long row
         const int64_t rs = a.ptr[r0], re = a.ptr[r0 + 1];
         const int64_t k0 = rs + (int64_t)U0.y * a.chunk;
         const int64_t k1 = k0 + a.chunk < re ? k0 + a.chunk : re;
         const double s = block_range_sum(a.idx, a.val, a.x, k0, k1, red);
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             const int32_t first = u - U0.y;
             const int32_t nch = (int32_t)((re - rs + a.chunk - 1) / a.chunk);
             a.partial[u] = s;
@@ -133,27 +146,73 @@ __device__ __forceinline__ void csr_unit(const CsrArgs& a, int32_t u, double* pr
     const int32_t nrows = r1 - r0;
     if (nrows == 1) {
         const double s = block_range_sum(a.idx, a.val, a.x, a.ptr[r0], a.ptr[r0 + 1], red);
-        if (threadIdx.x == 0) csr_put<ADD>(a, r0, s);
+        if (tid == 0) csr_put<ADD>(a, r0, s);
         __syncthreads();
         return;
     }
+    const int cap = 2 * block_nnz + 256;
+    double* sv = smem;
+    double* sx = smem + cap;
+    double* hv = smem + 2 * cap;
+    int32_t* sp = reinterpret_cast<int32_t*>(hv + 256);
+    int32_t* hr = sp + 260;
     const int64_t k0 = a.ptr[r0];
     const int32_t n = (int32_t)(a.ptr[r1] - k0);
 #pragma unroll 4
-    for (int32_t k = threadIdx.x; k < n; k += 256) prod[k] = __ldcs(a.val + k0 + k) * ldx(a.x, __ldcs(a.idx + k0 + k));
-    __syncthreads();
-    int T = 32;
-    while (T > 1 && T * nrows > 256) T >>= 1;
-    const int g = threadIdx.x / T, l = threadIdx.x & (T - 1);
-    double s = 0.0;
-    if (g < nrows) {
-        const int32_t rs = (int32_t)(a.ptr[r0 + g] - k0), re = (int32_t)(a.ptr[r0 + g + 1] - k0);
-        for (int32_t k = rs + l; k < re; k += T) s += prod[k];
+    for (int32_t k = tid; k < n; k += 256) {
+        sv[k] = __ldcs(a.val + k0 + k);
+        sx[k] = ldx(a.x, __ldcs(a.idx + k0 + k));
     }
-    for (int o = T >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-    if (g < nrows && l == 0) csr_put<ADD>(a, r0 + g, s);
+    for (int32_t t = tid; t <= nrows; t += 256) sp[t] = (int32_t)(a.ptr[r0 + t] - k0);
     __syncthreads();
-    (void)flag;
+    if (tid < nrows && sp[tid + 1] == sp[tid]) csr_put<ADD>(a, r0 + tid, 0.0);  // empty rows
+    const int32_t CT = ((n + 255) >> 8) | 1;
+    const int32_t c0 = tid * CT;
+    const int32_t c1 = c0 + CT < n ? c0 + CT : n;
+    double s = 0.0, head = 0.0;
+    int32_t head_row = -1, row = 0, owned_tail = -1;
+    if (c0 < c1) {
+        int32_t lo = 0, hi = nrows - 1;
+        while (lo < hi) {  // the row holding nonzero c0
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (sp[mid] <= c0) lo = mid;
+            else hi = mid - 1;
+        }
+        row = lo;
+        int32_t end = sp[row + 1];
+        bool own = sp[row] == c0;
+        for (int32_t k = c0; k < c1; ++k) {
+            if (k == end) {
+                if (own) csr_put<ADD>(a, r0 + row, s);
+                else { head = s; head_row = row; }
+                s = 0.0;
+                own = true;
+                do {
+                    ++row;
+                    end = sp[row + 1];
+                } while (end == k);
+            }
+            s = fma(sv[k], sx[k], s);
+        }
+        if (end == c1) {  // the current segment closes at the chunk end
+            if (own) csr_put<ADD>(a, r0 + row, s);
+            else { head = s; head_row = row; }
+        } else if (own) {
+            owned_tail = row;  // continues into later chunks
+        } else {
+            head = s;  // the whole chunk lies inside a row begun earlier
+            head_row = row;
+        }
+    }
+    hv[tid] = head;
+    hr[tid] = head_row;
+    __syncthreads();
+    if (owned_tail >= 0) {
+        double acc = s;
+        for (int t2 = tid + 1; t2 < 256 && hr[t2] == owned_tail; ++t2) acc += hv[t2];
+        csr_put<ADD>(a, r0 + owned_tail, acc);
+    }
+    __syncthreads();
 }
 
 // ------------------------------------------------------------------- ELL
@@ -354,8 +413,9 @@ __device__ __forceinline__ void csr5_tile(const Csr5Args& a, int64_t t, int lane
     int j = 0;  // segments of this lane seen so far
     for (int r = 0; r < a.sigma; ++r) {
         const int64_t slot = base + (int64_t)r * 32 + lane;
-        double p = 0.0;
-        if (kl + r < a.nnz) p = __ldcs(a.tile_val + slot) * ldx(a.x, __ldcs(a.tile_idx + slot));
+        const bool valid = kl + r < a.nnz;  // false only in the padded last tile
+        const double v = valid ? __ldcs(a.tile_val + slot) : 0.0;
+        const double xv = valid ? ldx(a.x, __ldcs(a.tile_idx + slot)) : 0.0;
         if ((f >> r) & 1u) {
             if (j == 0) {
                 head = cur;
@@ -368,16 +428,16 @@ __device__ __forceinline__ void csr5_tile(const Csr5Args& a, int64_t t, int lane
             ++j;
             cur = 0.0;
         }
-        cur += p;
+        cur = fma(v, xv, cur);  // one DFMA per nonzero
     }
     if (nf == 0) head = cur;
     // T_c = head_c + (lane c holds no flag ? T_{c+1} : 0)
     double T = head;
-    bool stop = nf > 0;
+    int stop = nf > 0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const double Tn = __shfl_down_sync(kFull, T, d);
-        const bool sn = __shfl_down_sync(kFull, stop, d);
+        const int sn = __shfl_down_sync(kFull, stop, d);
         if (!stop && lane + d < 32) {
             T += Tn;
             stop = sn;

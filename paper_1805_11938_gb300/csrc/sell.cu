@@ -103,7 +103,7 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     const int32_t m = c->m;
     int32_t C = h->params.sell_C ? h->params.sell_C : 32;
     if (C != 32 && C != 64 && C != 128) return set_error(SPMV_ERR_INVALID_ARG, "sell_C must be 32, 64 or 128 (got %d)", C);
-    int64_t sigma = h->params.sell_sigma ? h->params.sell_sigma : 32LL * C;
+    int64_t sigma = h->params.sell_sigma ? h->params.sell_sigma : (int64_t)m;
     if (sigma == SPMV_SELL_SIGMA_ALL || sigma > m) sigma = m;
     if (sigma < 1 || (sigma != 1 && sigma != m && sigma % C != 0))
         return set_error(SPMV_ERR_INVALID_ARG, "sell_sigma must be 1, a multiple of sell_C, or -1 (got %lld)",

@@ -1,0 +1,115 @@
+"""Training data for the format selector, collected on this GPU.
+
+Sec. V-B "Generating Training Data": every training matrix is run in every
+representation, repeating until the 95% confidence interval is within 5% of
+the mean, the best one is recorded as the label, and the static features are
+extracted.  Here the matrices are the seeded synthetic corpus (1000 matrices,
+n log-uniform in [1e3, 5e6], five structure families: banded, stencils,
+block-diagonal, uniform random, power-law rows) and every step runs in the
+library: conversion, spmv_features, and spmv_run timed with CUDA events after
+an L2 flush.
+
+One JSON line per matrix is appended to the output file, so an interrupted run
+resumes where it stopped (matrices already in the file are skipped).
+
+    python -m paper_1805_11938_gb300.profile_corpus --out table.jsonl [--count 1000]
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FORMAT_CAP_BYTES = 24 << 30  # a padded layout larger than this counts as infeasible (throughput 0)
+
+
+def done_indices(path: str) -> set:
+    out = set()
+    if os.path.exists(path):
+        with open(path) as f:
+            for line in f:
+                try:
+                    out.add(json.loads(line)["index"])
+                except (ValueError, KeyError):
+                    continue
+    return out
+
+
+def profile_one(a, spec, timer, cap_bytes: int, measure_kw: dict) -> dict:
+    import numpy as np
+    import torch
+
+    import synth
+    from . import FORMATS, DeviceCSR, SpmvError, spmv_convert, spmv_features, spmv_run
+
+    d = DeviceCSR.from_host(a)
+    feat = spmv_features(d).cpu().numpy().astype(float).tolist()
+    x = torch.as_tensor(synth.vector(a.n, spec["seed"] ^ 0x77)).cuda()
+    y = torch.empty(a.m, dtype=torch.float64, device="cuda")
+    times, status, conv = {}, {}, {}
+    for f in range(5):
+        try:
+            t0 = time.perf_counter()
+            h = spmv_convert(f, d, {"max_bytes": cap_bytes})
+            torch.cuda.synchronize()
+            conv[FORMATS[f]] = 1e3 * (time.perf_counter() - t0)
+        except SpmvError as e:
+            times[FORMATS[f]] = None
+            status[FORMATS[f]] = e.name
+            continue
+        r = timer.measure(lambda: spmv_run(h, x, y), **measure_kw)
+        times[FORMATS[f]] = r["ms"]
+        status[FORMATS[f]] = f"ci={r['ci_halfwidth_ms'] / r['ms']:.3f} n={r['n']}"
+        del h
+    feas = {k: v for k, v in times.items() if v is not None}
+    best = min(feas, key=lambda k: feas[k])
+    return {"index": spec["index"], "spec": {k: v for k, v in spec.items() if k != "seed"}, "m": a.m, "nnz": a.nnz,
+            "features": feat, "ms": times, "status": status, "convert_ms": conv, "label": FORMATS.index(best),
+            "best": best}
+
+
+def run(out: str, count: int = 1000, start: int = 0, cap_bytes: int = FORMAT_CAP_BYTES, n_min: int = 10,
+        n_max: int = 60, log=print) -> None:
+    import synth
+    from .autotune import Timer
+
+    have = done_indices(out)
+    todo = [i for i in range(start, count) if i not in have]
+    timer = Timer()
+    kw = {"n_min": n_min, "n_max": n_max, "warmup": 2}
+    t_start = time.time()
+    with cf.ThreadPoolExecutor(2) as ex, open(out, "a") as fh:
+        futs = {}
+        for j, i in enumerate(todo[:2]):
+            futs[i] = ex.submit(synth.corpus_matrix, i)
+        for j, i in enumerate(todo):
+            a = futs.pop(i).result()
+            if j + 2 < len(todo):
+                futs[todo[j + 2]] = ex.submit(synth.corpus_matrix, todo[j + 2])
+            rec = profile_one(a, synth.corpus_spec(i), timer, cap_bytes, kw)
+            fh.write(json.dumps(rec) + "\n")
+            fh.flush()
+            if j % 50 == 0:
+                log(f"[{j + 1}/{len(todo)}] matrix {i} {rec['spec']['family']} n={a.m} nnz={a.nnz} best={rec['best']} "
+                    f"({time.time() - t_start:.0f} s)")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--count", type=int, default=1000)
+    ap.add_argument("--start", type=int, default=0)
+    ap.add_argument("--cap-gb", type=float, default=24.0)
+    args = ap.parse_args()
+    run(args.out, args.count, args.start, int(args.cap_gb * (1 << 30)))
+
+
+if __name__ == "__main__":
+    main()
