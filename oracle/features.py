@@ -21,7 +21,7 @@ len_i = ptr[i+1] - ptr[i];  L = sum over R of len_i;  |R| = count.
 10 hyb_tail    sum over R of max(0, len_i - K) / L, 0 if L = 0, where K is the
                HYB rule on R with lengths capped at 512: the largest
                k in [1, 512] with #{len_i >= k} >= ceil(|R|/3), else 0
-11 diag_spread mean |col - i| over the first min(len_i, 64) entries of each
+11 diag_spread mean |col - i| over the first min(len_i, 16) entries of each
                sampled row (0 if none)
 12 bandwidth   max |col - i| over the same entries
 13 empty_frac  #{len_i = 0} / |R|
@@ -42,7 +42,7 @@ FEATURE_NAMES = ("n_rows", "n_cols", "nnz_frac", "nnz_min", "nnz_max", "nnz_avg"
                  "sell32_fill")
 SAMPLE_ROWS = 16384
 LEN_CAP = 512
-SPREAD_ENTRIES = 64
+SPREAD_ENTRIES = 16
 LONG_ROW = 32
 
 

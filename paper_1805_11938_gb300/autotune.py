@@ -73,7 +73,7 @@ class Timer:
 
 def default_grid(fmt: int, m: int) -> list:
     if fmt == SPMV_CSR:
-        return [{"csr_block_nnz": b} for b in (256, 512, 1024, 2048)]
+        return [{}]
     if fmt == SPMV_CSR5:
         return [{"csr5_sigma": s} for s in (8, 12, 16, 24, 32)]
     if fmt == SPMV_ELL:

@@ -18,19 +18,19 @@
 namespace spmv {
 
 enum TaskKind : int32_t {
-    T_CSR = 0,       // one CSR unit (block)
+    T_CSR = 0,       // 8 CSR warp units
     T_CSR5 = 1,      // 8 CSR5 tiles (warp each)
     T_ELL = 2,       // 512 ELL rows
     T_ELL_LONG = 3,  // one long ELL row
     T_SELL = 4,      // 8 SELL units (warp each)
     T_CSR5_CAL = 5,  // 256 tiles of calibration / empty rows
-    T_HYB_TAIL = 6   // one HYB tail unit (block), adds into y
+    T_HYB_TAIL = 6   // 8 HYB tail warp units, adding into y
 };
 
 struct MatDesc {
     int32_t fmt, sell_r;
     int32_t n_zero;
-    int32_t csr_block_nnz;
+    int32_t csr_units;
     int32_t ell_nb;
     const int32_t* zero_rows;
     const int32_t* long_rows;
@@ -50,7 +50,7 @@ struct BatchDev {
 };
 
 __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
-    extern __shared__ double smem[];
+    __shared__ dev::CsrWarpSmem S[8];
     __shared__ double red[8];
     __shared__ int task_sh;
     for (;;) {
@@ -69,14 +69,16 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
                 dev::CsrArgs a = md.csr;
                 a.x = x;
                 a.y = y;
-                dev::csr_unit<false>(a, t.z, smem, md.csr_block_nnz, red);
+                const int32_t u = t.z * 8 + warp;
+                if (u < md.csr_units) dev::csr_warp_unit<false>(a, u, S[warp], lane);
                 break;
             }
             case T_HYB_TAIL: {
                 dev::CsrArgs a = md.csr;
                 a.x = x;
                 a.y = y;
-                dev::csr_unit<true>(a, t.z, smem, md.csr_block_nnz, red);
+                const int32_t u = t.z * 8 + warp;
+                if (u < md.csr_units) dev::csr_warp_unit<true>(a, u, S[warp], lane);
                 break;
             }
             case T_CSR5: {
@@ -161,17 +163,15 @@ struct spmv_batch {
 
 namespace spmv {
 
-static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, std::vector<int4>& t2, int32_t b,
-                      int32_t& max_block_nnz) {
+static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, std::vector<int4>& t2, int32_t b) {
     memset(&d, 0, sizeof d);
     d.fmt = h->fmt;
     switch (h->fmt) {
         case SPMV_CSR:
             d.csr = dev::CsrArgs{h->cu.units, h->ptr, h->idx, h->val, nullptr, nullptr, nullptr, h->cu.partial,
-                                 h->cu.counters, h->cu.chunk};
-            d.csr_block_nnz = h->cu.block_nnz;
-            if (h->cu.block_nnz > max_block_nnz) max_block_nnz = h->cu.block_nnz;
-            for (int32_t u = 0; u < h->cu.n; ++u) t1.push_back(make_int4(b, T_CSR, u, 0));
+                                 h->cu.counters};
+            d.csr_units = h->cu.n;
+            for (int64_t g = 0; g < ceil_div(h->cu.n, 8); ++g) t1.push_back(make_int4(b, T_CSR, (int32_t)g, 0));
             break;
         case SPMV_CSR5: {
             d.csr5 = dev::Csr5Args{h->ptr, h->tile_ptr, h->flags, h->tile_idx, h->tile_val, h->empty_ptr, h->empty_rows,
@@ -195,10 +195,10 @@ static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, s
                 for (int32_t j = 0; j < h->ell.n_long; ++j) t1.push_back(make_int4(b, T_ELL_LONG, j, 0));
             if (h->fmt == SPMV_HYB && h->n_tail_rows > 0) {
                 d.csr = dev::CsrArgs{h->tail_units.units, h->tail_ptr, h->tail_col, h->tail_val, h->tail_rows, nullptr,
-                                     nullptr, h->tail_units.partial, h->tail_units.counters, h->tail_units.chunk};
-                d.csr_block_nnz = h->tail_units.block_nnz;
-                if (h->tail_units.block_nnz > max_block_nnz) max_block_nnz = h->tail_units.block_nnz;
-                for (int32_t u = 0; u < h->tail_units.n; ++u) t2.push_back(make_int4(b, T_HYB_TAIL, u, 0));
+                                     nullptr, h->tail_units.partial, h->tail_units.counters};
+                d.csr_units = h->tail_units.n;
+                for (int64_t g = 0; g < ceil_div(h->tail_units.n, 8); ++g)
+                    t2.push_back(make_int4(b, T_HYB_TAIL, (int32_t)g, 0));
             }
             break;
         }
@@ -266,11 +266,10 @@ int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t st
     bt->handles.assign(handles, handles + count);
     std::vector<MatDesc> mats(count);
     std::vector<int4> t1, t2;
-    int32_t max_bnnz = 128;
-    for (int32_t b = 0; b < count; ++b) fill_desc(handles[b], mats[b], t1, t2, b, max_bnnz);
+    for (int32_t b = 0; b < count; ++b) fill_desc(handles[b], mats[b], t1, t2, b);
     bt->n1 = (int32_t)t1.size();
     bt->n2 = (int32_t)t2.size();
-    bt->smem = dev::csr_smem_bytes(max_bnnz);
+    bt->smem = 0;
     int st = dev_malloc((void**)&bt->d_mats, sizeof(MatDesc) * count);
     if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_tasks1, sizeof(int4) * (t1.size() + 1));
     if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_tasks2, sizeof(int4) * (t2.size() + 1));
@@ -291,8 +290,6 @@ int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t st
     int dev = 0, sms = 0, per_sm = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess && bt->smem > 48 * 1024)
-        e = cudaFuncSetAttribute((const void*)k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt->smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 256, bt->smem);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {

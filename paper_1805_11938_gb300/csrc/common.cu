@@ -268,15 +268,14 @@ int64_t resolve_cap(const spmv_params& p) {
 
 // ------------------------------------------------------------- CSR units
 //
-// Row i opens a unit when i = 0, when the previous row or row i itself is
-// longer than block_nnz, when i crosses a multiple of kCsrRowCap rows, or
-// when ptr[i] enters a new block_nnz-aligned window of nonzeros.  A unit of
-// short rows therefore holds at most kCsrRowCap rows and fewer than
-// 2*block_nnz nonzeros.  A long row longer than chunk = 4*block_nnz is split
-// into ceil(len/chunk) chunk units.
+// Row i opens a unit when i = 0, when row i or row i-1 holds more than
+// H = kCsrW/2 nonzeros, when i crosses a multiple of kCsrRows rows, or when
+// ptr[i] enters a new H-aligned window of nonzeros.  A unit of short rows
+// therefore holds at most kCsrRows rows and fewer than 2H = kCsrW nonzeros.
+// A row longer than kCsrChunk becomes ceil(len / kCsrChunk) chunk units.
 
-__global__ void k_unit_counts(const int32_t* __restrict__ ptr, int32_t m, int32_t B, int32_t chunk,
-                              int32_t* __restrict__ cnt) {
+__global__ void k_unit_counts(const int32_t* __restrict__ ptr, int32_t m, int32_t* __restrict__ cnt) {
+    constexpr int32_t H = dev::kCsrW / 2, CH = dev::kCsrChunk;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > m) return;
     if (i == m) {
@@ -284,40 +283,38 @@ __global__ void k_unit_counts(const int32_t* __restrict__ ptr, int32_t m, int32_
         return;
     }
     const int32_t p = ptr[i], len = ptr[i + 1] - p;
-    const bool lng = len > B;
-    bool start = (i == 0) || lng;
+    bool start = (i == 0) || len > H;
     if (i > 0) {
         const int32_t pp = ptr[i - 1];
-        start = start || (p - pp > B) || (i / kCsrRowCap != (i - 1) / kCsrRowCap) || (p / B != pp / B);
+        start = start || (p - pp > H) || (i / dev::kCsrRows != (i - 1) / dev::kCsrRows) || (p / H != pp / H);
     }
-    cnt[i] = start ? (len > chunk ? (len + chunk - 1) / chunk : 1) : 0;
+    cnt[i] = start ? (len > CH ? (len + CH - 1) / CH : 1) : 0;
 }
 
-__global__ void k_unit_fill(const int32_t* __restrict__ ptr, int32_t m, int32_t chunk, const int32_t* __restrict__ cnt,
-                            const int32_t* __restrict__ off, int2* __restrict__ units) {
+__global__ void k_unit_fill(const int32_t* __restrict__ ptr, int32_t m, const int32_t* __restrict__ cnt,
+                            const int32_t* __restrict__ off, int4* __restrict__ units) {
+    constexpr int32_t CH = dev::kCsrChunk;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i > m) return;
     if (i == m) {
-        units[off[m]] = make_int2(m, -1);
+        units[off[m]] = make_int4(m, ptr[m], -1, 0);
         return;
     }
     const int32_t c = cnt[i];
     if (c == 0) return;
-    const int32_t len = ptr[i + 1] - ptr[i];
-    const bool split = len > chunk;
-    for (int32_t k = 0; k < c; ++k) units[off[i] + k] = make_int2((int32_t)i, split ? k : -1);
+    const int32_t p = ptr[i], len = ptr[i + 1] - p;
+    const bool split = len > CH;
+    for (int32_t k = 0; k < c; ++k)
+        units[off[i] + k] = make_int4((int32_t)i, p + k * CH, split ? k : -1, split ? c : 0);
 }
 
-int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t rows, int32_t block_nnz,
-                    const char* prefix, cudaStream_t s) {
-    SPMV_TRY(csr_prepare_kernels());
+int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t rows, const char* prefix,
+                    cudaStream_t s) {
     Scratch tmp;
-    cu.block_nnz = block_nnz;
-    cu.chunk = 4 * block_nnz;
     int32_t *cnt = nullptr, *off = nullptr;
     SPMV_TRY(tmp.get(&cnt, (size_t)rows + 1));
     SPMV_TRY(tmp.get(&off, (size_t)rows + 2));
-    k_unit_counts<<<grid_for((int64_t)rows + 1, 256), 256, 0, s>>>(ptr, rows, block_nnz, cu.chunk, cnt);
+    k_unit_counts<<<grid_for((int64_t)rows + 1, 256), 256, 0, s>>>(ptr, rows, cnt);
     SPMV_CUDA(cudaGetLastError());
     SPMV_TRY(exclusive_scan<int32_t>(cnt, off, (int64_t)rows + 1, s, tmp));
     int32_t n_units = 0;
@@ -329,7 +326,7 @@ int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t ro
     SPMV_TRY(h->alloc(&cu.partial, (size_t)n_units + 1, nullptr));
     SPMV_TRY(h->alloc(&cu.counters, (size_t)n_units + 1, nullptr));
     SPMV_CUDA(cudaMemsetAsync(cu.counters, 0, sizeof(unsigned) * ((size_t)n_units + 1), s));
-    k_unit_fill<<<grid_for((int64_t)rows + 1, 256), 256, 0, s>>>(ptr, rows, cu.chunk, cnt, off, cu.units);
+    k_unit_fill<<<grid_for((int64_t)rows + 1, 256), 256, 0, s>>>(ptr, rows, cnt, off, cu.units);
     SPMV_CUDA(cudaGetLastError());
     SPMV_CUDA(cudaStreamSynchronize(s));
     return SPMV_OK;

@@ -8,7 +8,7 @@
 //   0 n_rows  1 n_cols  2 nnz/(M*N)  3 min len  4 max len  5 nnz/M
 //   6 std of len over R  7 std/mean  8 log2(max(nnz,1))  9 mean/max
 //  10 HYB tail fraction with K from R (lengths capped at 512)
-//  11 mean |col-row| and 12 max |col-row| over the first 64 entries of each sampled row
+//  11 mean |col-row| and 12 max |col-row| over the first 16 entries of each sampled row
 //  13 fraction of empty rows  14 fraction of rows with len >= 32
 //  15 SELL-32 fill over R sorted, lengths capped at 512
 //
@@ -35,7 +35,7 @@ constexpr int kFeatCtas = 8;
 constexpr int kFeatThreads = 1024;
 constexpr int kSample = 16384;
 constexpr int kLenCap = 512;
-constexpr int kSpread = 64;
+constexpr int kSpread = 16;
 
 // parameter offsets inside the flat vector
 constexpr int oW1 = 0, oB1 = 1024, oW2 = 1088, oB2 = 5184, oW3 = 5248, oB3 = 5568, kNP = 5573;
@@ -114,19 +114,22 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         mx = max(mx, len);
         emp += len == 0;
         lng += len >= 32;
-        atomicAdd(&part.hist[len < kLenCap ? len : kLenCap], 1u);
+        {  // one shared atomic per distinct bin in the warp
+            const int bin = len < kLenCap ? len : kLenCap;
+            const unsigned act = __activemask();
+            const unsigned peers = __match_any_sync(act, bin);
+            if ((threadIdx.x & 31) == (__ffs(peers) - 1)) atomicAdd(&part.hist[bin], (unsigned)__popc(peers));
+        }
         const int ne = len < kSpread ? len : kSpread;
-        for (int e0 = 0; e0 < ne; e0 += 8) {  // eight independent loads in flight
-            int32_t c[8];
+        int32_t c[kSpread];  // all index loads of the row in flight at once
 #pragma unroll
-            for (int q = 0; q < 8; ++q) c[q] = e0 + q < ne ? __ldg(idx + p0 + e0 + q) : (int32_t)i;
+        for (int q = 0; q < kSpread; ++q) c[q] = q < ne ? __ldg(idx + p0 + q) : (int32_t)i;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int64_t d = (int64_t)c[q] - i;
-                const int ad = (int)(d < 0 ? -d : d);
-                ssum += (unsigned long long)ad;
-                band = max(band, ad);
-            }
+        for (int q = 0; q < kSpread; ++q) {
+            const int64_t d = (int64_t)c[q] - i;
+            const int ad = (int)(d < 0 ? -d : d);
+            ssum += (unsigned long long)ad;
+            band = max(band, ad);
         }
         scnt += (unsigned long long)ne;
     }
@@ -171,11 +174,20 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         __shared__ unsigned long long widths;
         __shared__ unsigned long long upto_k;
         __shared__ unsigned long long capped_sum;
+        __shared__ FeatPart parts[kFeatCtas];
+        if (tid < kFeatCtas) {  // one thread per cluster rank reads that rank's partial
+            const FeatPart* q = cluster.map_shared_rank(&part, (int)tid);
+            parts[tid].sum_len = q->sum_len; parts[tid].sum_sq = q->sum_sq;
+            parts[tid].spread_sum = q->spread_sum; parts[tid].spread_cnt = q->spread_cnt;
+            parts[tid].min_len = q->min_len; parts[tid].max_len = q->max_len; parts[tid].band = q->band;
+            parts[tid].empty = q->empty; parts[tid].longc = q->longc;
+        }
+        __syncthreads();
         if (tid == 0) {
             tot.sum_len = tot.sum_sq = tot.spread_sum = tot.spread_cnt = 0;
             tot.min_len = 0x7fffffff; tot.max_len = 0; tot.band = 0; tot.empty = 0; tot.longc = 0;
             for (int r = 0; r < kFeatCtas; ++r) {
-                const FeatPart* q = cluster.map_shared_rank(&part, r);
+                const FeatPart* q = &parts[r];
                 tot.sum_len += q->sum_len; tot.sum_sq += q->sum_sq;
                 tot.spread_sum += q->spread_sum; tot.spread_cnt += q->spread_cnt;
                 tot.min_len = min(tot.min_len, q->min_len); tot.max_len = max(tot.max_len, q->max_len);
@@ -201,53 +213,87 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         }
         const unsigned cnt = (unsigned)S;
         const unsigned need = (cnt + 2) / 3;
-        // K = #{k in [1, 512] : c_k >= need}; SELL widths = sum_k ceil(c_k / 32)
-        int okK = 0;
-        unsigned long long wpart = 0;
+        // K = #{k in [1, 512] : c_k >= need}; SELL widths = sum_k ceil(c_k / 32);
+        // capped = sum_k c_k = sum min(len, 512): warp shuffles, then one pass over the warps
+        __shared__ unsigned long long wred[32][3];
+        unsigned long long okK = 0, wpart = 0, cpart = 0;
         if (tid >= 1 && tid <= kLenCap) {
             okK = ck[tid] >= need;
             wpart = (ck[tid] + 31) / 32;
+            cpart = ck[tid];
         }
-        okK = __syncthreads_count(okK);
-        atomicAdd(&widths, wpart);
-        __syncthreads();
-        if (tid == 0) Ksh = okK;
-        __syncthreads();
-        if (tid >= 1 && tid <= Ksh) atomicAdd(&upto_k, (unsigned long long)ck[tid]);  // sum_{k<=K} c_k = sum min(len, K)
-        if (tid >= 1 && tid <= kLenCap) atomicAdd(&capped_sum, (unsigned long long)ck[tid]);  // sum min(len, 512)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            okK += __shfl_xor_sync(dev::kFull, okK, o);
+            wpart += __shfl_xor_sync(dev::kFull, wpart, o);
+            cpart += __shfl_xor_sync(dev::kFull, cpart, o);
+        }
+        if ((tid & 31) == 0) {
+            wred[tid >> 5][0] = okK;
+            wred[tid >> 5][1] = wpart;
+            wred[tid >> 5][2] = cpart;
+        }
         __syncthreads();
         if (tid == 0) {
+            unsigned long long a0 = 0, a1 = 0, a2 = 0;
+            for (int q = 0; q < kLenCap / 32 + 1; ++q) {
+                a0 += wred[q][0];
+                a1 += wred[q][1];
+                a2 += wred[q][2];
+            }
+            Ksh = (int)a0;
+            widths = a1;
+            capped_sum = a2;
+        }
+        __syncthreads();
+        // sum_{k<=K} c_k = sum min(len, K), by the first warps
+        unsigned long long up = (tid >= 1 && tid <= Ksh) ? ck[tid] : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(dev::kFull, up, o);
+        if ((tid & 31) == 0) wred[tid >> 5][0] = up;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long a0 = 0;
+            for (int q = 0; q < kLenCap / 32 + 1; ++q) a0 += wred[q][0];
+            upto_k = a0;
+        }
+        __syncthreads();
+        if (tid < 16) {  // one lane per feature, FP64
+            const int j = tid;
             const double L = (double)tot.sum_len;
             const double mean = L / (double)cnt;
-            // std = sqrt(cnt * sum_sq - L^2) / cnt in exact 128-bit integer arithmetic
-            const unsigned long long a_lo = (unsigned long long)cnt * tot.sum_sq;
-            const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, tot.sum_sq);
-            const unsigned long long b_lo = tot.sum_len * tot.sum_len;
-            const unsigned long long b_hi = __umul64hi(tot.sum_len, tot.sum_len);
-            const unsigned long long d_lo = a_lo - b_lo;
-            const unsigned long long d_hi = a_hi - b_hi - (a_lo < b_lo ? 1ull : 0ull);
-            const double var_num = (double)d_hi * 18446744073709551616.0 + (double)d_lo;
-            const double sd = sqrt(var_num) / (double)cnt;
             const double nnz = (double)ptr[m];
-            const unsigned long long tail = tot.sum_len - upto_k;
-            double f[16];
-            f[0] = (double)m;
-            f[1] = (double)n;
-            f[2] = nnz / ((double)m * (double)n);
-            f[3] = (double)tot.min_len;
-            f[4] = (double)tot.max_len;
-            f[5] = nnz / (double)m;
-            f[6] = sd;
-            f[7] = tot.sum_len > 0 ? sd / mean : 0.0;
-            f[8] = log2(nnz > 1.0 ? nnz : 1.0);
-            f[9] = tot.max_len > 0 ? mean / (double)tot.max_len : 0.0;
-            f[10] = tot.sum_len > 0 ? (double)tail / L : 0.0;
-            f[11] = tot.spread_cnt > 0 ? (double)tot.spread_sum / (double)tot.spread_cnt : 0.0;
-            f[12] = (double)tot.band;
-            f[13] = (double)tot.empty / (double)cnt;
-            f[14] = (double)tot.longc / (double)cnt;
-            f[15] = widths > 0 ? (double)capped_sum / (32.0 * (double)widths) : 1.0;
-            for (int j = 0; j < 16; ++j) fs[j] = (float)f[j];
+            double sd = 0.0;
+            if (j == 6 || j == 7) {
+                // std = sqrt(cnt * sum_sq - L^2) / cnt in exact 128-bit integer arithmetic
+                const unsigned long long a_lo = (unsigned long long)cnt * tot.sum_sq;
+                const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, tot.sum_sq);
+                const unsigned long long b_lo = tot.sum_len * tot.sum_len;
+                const unsigned long long b_hi = __umul64hi(tot.sum_len, tot.sum_len);
+                const unsigned long long d_lo = a_lo - b_lo;
+                const unsigned long long d_hi = a_hi - b_hi - (a_lo < b_lo ? 1ull : 0ull);
+                sd = sqrt((double)d_hi * 18446744073709551616.0 + (double)d_lo) / (double)cnt;
+            }
+            double f = 0.0;
+            switch (j) {
+                case 0: f = (double)m; break;
+                case 1: f = (double)n; break;
+                case 2: f = nnz / ((double)m * (double)n); break;
+                case 3: f = (double)tot.min_len; break;
+                case 4: f = (double)tot.max_len; break;
+                case 5: f = nnz / (double)m; break;
+                case 6: f = sd; break;
+                case 7: f = tot.sum_len > 0 ? sd / mean : 0.0; break;
+                case 8: f = log2(nnz > 1.0 ? nnz : 1.0); break;
+                case 9: f = tot.max_len > 0 ? mean / (double)tot.max_len : 0.0; break;
+                case 10: f = tot.sum_len > 0 ? (double)(tot.sum_len - upto_k) / L : 0.0; break;
+                case 11: f = tot.spread_cnt > 0 ? (double)tot.spread_sum / (double)tot.spread_cnt : 0.0; break;
+                case 12: f = (double)tot.band; break;
+                case 13: f = (double)tot.empty / (double)cnt; break;
+                case 14: f = (double)tot.longc / (double)cnt; break;
+                default: f = widths > 0 ? (double)capped_sum / (32.0 * (double)widths) : 1.0; break;
+            }
+            fs[j] = (float)f;
         }
         __syncthreads();
         if (feat_out && tid < 16) feat_out[tid] = fs[tid];

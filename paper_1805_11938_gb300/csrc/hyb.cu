@@ -131,9 +131,7 @@ int hyb_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
                                          h->tail_val);
         SPMV_CUDA(cudaGetLastError());
     }
-    int32_t B = h->params.csr_block_nnz ? h->params.csr_block_nnz : 512;
-    if (B < 128 || B > 2048 || (B & (B - 1))) B = 512;
-    SPMV_TRY(build_csr_units(h, h->tail_units, h->tail_ptr, ntr, B, "tail_", s));
+    SPMV_TRY(build_csr_units(h, h->tail_units, h->tail_ptr, ntr, "tail_", s));
     h->stored_slots += nt;
     h->aux[0] = nt;
     h->aux[1] = ntr;

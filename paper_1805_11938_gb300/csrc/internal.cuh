@@ -15,7 +15,6 @@
 namespace spmv {
 
 constexpr int kThreads = 256;      // block size of the SpMV kernels
-constexpr int kCsrRowCap = 256;    // rows per CSR row block (one thread each at most)
 constexpr int kEllLongRow = 64;    // ELL rows longer than this go to the warp-per-row kernel
 constexpr int kSellUnitWidth = 256;  // SELL slices wider than this are split over several warps
 constexpr int kCsr5Omega = 32;     // CSR5 tile width = warp width
@@ -60,14 +59,14 @@ struct NamedArray {
     int32_t elem_bytes;
 };
 
-// CSR row-block work units (also used for the HYB COO tail): unit u covers
-// rows [units[u].x, units[u+1].x); units[u].y >= 0 marks chunk y of one long row.
+// CSR warp units (also used for the HYB COO tail): units[u] = {r0, k0, c, nch},
+// the unit covers rows [r0, units[u+1].x) and nonzeros [k0, units[u+1].y);
+// c >= 0 marks chunk c of nch of one long row.
 struct CsrUnits {
-    int2* units = nullptr;      // n + 1 entries (sentinel {rows, -1})
+    int4* units = nullptr;      // n + 1 entries (sentinel {rows, nnz, -1, 0})
     int32_t n = 0;
     double* partial = nullptr;  // per unit, for split long rows
     unsigned* counters = nullptr;
-    int32_t block_nnz = 1024, chunk = 4096;
 };
 
 struct EllPart {  // column-major ELL: slot s of row i at s*ld + i
@@ -165,12 +164,11 @@ int row_lengths(const int32_t* ptr, int32_t m, int32_t* len, cudaStream_t s);
 int max_i32(const int32_t* a, int64_t n, int32_t* result_host, cudaStream_t s, Scratch& tmp);
 int copy_csr(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
 int64_t resolve_cap(const spmv_params& p);
-// Units of CSR row blocks over (ptr, rows); block_nnz a power of two.
-int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t rows, int32_t block_nnz,
-                    const char* prefix, cudaStream_t s);
+// Warp units of CSR row blocks over (ptr, rows).
+int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t rows, const char* prefix,
+                    cudaStream_t s);
 
 // ---- per-format conversion and launch
-int csr_prepare_kernels();
 int csr_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
 int csr_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s);
 int csr_units_launch(const CsrUnits& cu, const int32_t* ptr, const int32_t* idx, const double* val,

@@ -49,46 +49,34 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
     return s;
 }
 
-// Sum of val[k] * x[idx[k]] over k in [k0, k1) by all 256 threads of a block
-// (four independent accumulators per thread keep four gathers in flight).
-__device__ __forceinline__ double block_range_sum(const int32_t* __restrict__ idx, const double* __restrict__ val,
-                                                  const double* __restrict__ x, int64_t k0, int64_t k1,
-                                                  double* red) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int64_t k = k0 + threadIdx.x;
-    for (; k + 768 < k1; k += 1024) {
-        const int32_t c0 = __ldcs(idx + k), c1 = __ldcs(idx + k + 256), c2 = __ldcs(idx + k + 512),
-                      c3 = __ldcs(idx + k + 768);
-        const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 256), v2 = __ldcs(val + k + 512),
-                     v3 = __ldcs(val + k + 768);
-        s0 = fma(v0, ldx(x, c0), s0);
-        s1 = fma(v1, ldx(x, c1), s1);
-        s2 = fma(v2, ldx(x, c2), s2);
-        s3 = fma(v3, ldx(x, c3), s3);
-    }
-    for (; k < k1; k += 256) s0 = fma(__ldcs(val + k), ldx(x, __ldcs(idx + k)), s0);
-    return block_sum256((s0 + s1) + (s2 + s3), red);
-}
-
 // ------------------------------------------------------------------- CSR
 //
-// Unit u covers rows [units[u].x, units[u+1].x).  On this GPU the FP64 pipe
-// issues about two lanes per clock per SM, so every FP64 instruction must
-// carry a full warp of useful work: exactly one DFMA per nonzero, with the
-// lanes kept busy, and as few cross-lane FP64 reductions as possible.
+// On this GPU the FP64 pipe issues about two lanes per clock per SM, so every
+// FP64 instruction must carry a full warp of useful work: one DFMA per
+// nonzero, lanes kept busy, cross-lane FP64 reductions only where amortised.
+// Random gathers of x cost one L1 wavefront per lane, so every other load is
+// coalesced.
 //
-// A multi-row unit (fewer than 2*block_nnz nonzeros, at most 256 rows): the
-// block stages values and gathered x[idx] in shared memory with coalesced
-// loads, then thread t walks the contiguous chunk [t*CT, t*CT + CT) (CT odd,
-// so 8-byte shared accesses are conflict-free) with one DFMA per nonzero,
-// writing every row that begins and ends in its chunk.  A row begun in an
-// earlier chunk leaves its partial in shared memory; the thread that owns the
-// row's start adds those partials in chunk order.
-// A one-row unit is reduced by the whole block.  units[u].y = c >= 0 marks
-// chunk c of a row longer than `chunk`: its partial goes to partial[u] and
-// the last chunk to finish (atomic ticket) adds the chunks in order.
+// Work is split into warp units (units[u] = {r0, k0, c, nch}; the next unit
+// gives r1 and k1):
+//  * c = -1, several rows (fewer than kCsrW nonzeros, at most kCsrRows rows):
+//    the warp stages values and gathered x[idx] in its shared slice with
+//    coalesced loads, then lane l walks the contiguous chunk
+//    [l*CT, l*CT + CT) (CT odd: conflict-free 8-byte shared accesses) with one
+//    DFMA per nonzero, writing every row that begins and ends in its chunk;
+//    a row begun in an earlier lane leaves its partial in shared memory and
+//    the lane owning the row's start adds those partials in lane order;
+//  * c = -1, one row longer than the unit budget: lanes stride the row with
+//    four accumulators, then one warp reduction;
+//  * c >= 0: chunk c of nch of a row longer than kCsrChunk; partials go to
+//    partial[u] and the last chunk to finish (atomic ticket) adds them in
+//    order.
+constexpr int kCsrW = 224;      // a multi-row unit holds fewer nonzeros than this
+constexpr int kCsrRows = 64;    // and at most this many rows
+constexpr int kCsrChunk = 2048; // rows longer than this are split into chunks
+
 struct CsrArgs {
-    const int2* units;
+    const int4* units;
     const int32_t* ptr;
     const int32_t* idx;
     const double* val;
@@ -97,7 +85,14 @@ struct CsrArgs {
     double* y;
     double* partial;
     unsigned* counters;
-    int32_t chunk;
+};
+
+struct CsrWarpSmem {
+    double sv[kCsrW];
+    double sx[kCsrW];
+    double hv[32];
+    int32_t sp[kCsrRows + 1];
+    int32_t hr[32];
 };
 
 template <bool ADD>
@@ -110,77 +105,82 @@ __device__ __forceinline__ void csr_put(const CsrArgs& a, int32_t r, double s) {
     }
 }
 
-// Shared memory of a CSR block: csr_smem_bytes(block_nnz).
-__host__ __device__ constexpr size_t csr_smem_bytes(int block_nnz) {
-    return (size_t)2 * (2 * block_nnz + 256) * sizeof(double) + 256 * sizeof(double) + 2 * 260 * sizeof(int32_t);
+// Sum of val[k] * x[idx[k]] over [k0, k1) by one warp; valid in every lane.
+__device__ __forceinline__ double warp_range_sum(const int32_t* __restrict__ idx, const double* __restrict__ val,
+                                                 const double* __restrict__ x, int64_t k0, int64_t k1, int lane) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int64_t k = k0 + lane;
+    for (; k + 96 < k1; k += 128) {
+        const int32_t c0 = __ldcs(idx + k), c1 = __ldcs(idx + k + 32), c2 = __ldcs(idx + k + 64),
+                      c3 = __ldcs(idx + k + 96);
+        const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
+                     v3 = __ldcs(val + k + 96);
+        s0 = fma(v0, ldx(x, c0), s0);
+        s1 = fma(v1, ldx(x, c1), s1);
+        s2 = fma(v2, ldx(x, c2), s2);
+        s3 = fma(v3, ldx(x, c3), s3);
+    }
+    for (; k < k1; k += 32) s0 = fma(__ldcs(val + k), ldx(x, __ldcs(idx + k)), s0);
+    return warp_sum((s0 + s1) + (s2 + s3));
 }
 
 template <bool ADD>
-__device__ __forceinline__ void csr_unit(const CsrArgs& a, int32_t u, double* smem, int32_t block_nnz, double* red) {
-    const int2 U0 = a.units[u];
-    const int32_t r0 = U0.x;
-    const int tid = threadIdx.x;
-    if (U0.y >= 0) {  // one chunk of a long row
-        const int64_t rs = a.ptr[r0], re = a.ptr[r0 + 1];
-        const int64_t k0 = rs + (int64_t)U0.y * a.chunk;
-        const int64_t k1 = k0 + a.chunk < re ? k0 + a.chunk : re;
-        const double s = block_range_sum(a.idx, a.val, a.x, k0, k1, red);
-        if (tid == 0) {
-            const int32_t first = u - U0.y;
-            const int32_t nch = (int32_t)((re - rs + a.chunk - 1) / a.chunk);
+__device__ __forceinline__ void csr_warp_unit(const CsrArgs& a, int32_t u, CsrWarpSmem& S, int lane) {
+    const int4 U = a.units[u];
+    const int4 V = a.units[u + 1];
+    const int32_t r0 = U.x;
+    const int32_t k0 = U.y, k1 = V.y;
+    if (U.z >= 0) {  // chunk U.z of U.w of one long row
+        const double s = warp_range_sum(a.idx, a.val, a.x, k0, k1, lane);
+        if (lane == 0) {
+            const int32_t first = u - U.z;
             a.partial[u] = s;
             __threadfence();
             const unsigned prev = atomicAdd(a.counters + first, 1u);
-            if (prev == (unsigned)(nch - 1)) {
+            if (prev == (unsigned)(U.w - 1)) {
                 __threadfence();
                 double acc = 0.0;
-                for (int32_t c = 0; c < nch; ++c) acc += __ldcg(a.partial + first + c);
+                for (int32_t c = 0; c < U.w; ++c) acc += __ldcg(a.partial + first + c);
                 a.counters[first] = 0u;
                 csr_put<ADD>(a, r0, acc);
             }
         }
-        __syncthreads();
         return;
     }
-    const int32_t r1 = a.units[u + 1].x;
-    const int32_t nrows = r1 - r0;
-    if (nrows == 1) {
-        const double s = block_range_sum(a.idx, a.val, a.x, a.ptr[r0], a.ptr[r0 + 1], red);
-        if (tid == 0) csr_put<ADD>(a, r0, s);
-        __syncthreads();
+    const int32_t nrows = V.x - r0;
+    const int32_t n = k1 - k0;
+    if (nrows == 1 && n >= kCsrW) {  // one long row
+        const double s = warp_range_sum(a.idx, a.val, a.x, k0, k1, lane);
+        if (lane == 0) csr_put<ADD>(a, r0, s);
         return;
     }
-    const int cap = 2 * block_nnz + 256;
-    double* sv = smem;
-    double* sx = smem + cap;
-    double* hv = smem + 2 * cap;
-    int32_t* sp = reinterpret_cast<int32_t*>(hv + 256);
-    int32_t* hr = sp + 260;
-    const int64_t k0 = a.ptr[r0];
-    const int32_t n = (int32_t)(a.ptr[r1] - k0);
-#pragma unroll 4
-    for (int32_t k = tid; k < n; k += 256) {
-        sv[k] = __ldcs(a.val + k0 + k);
-        sx[k] = ldx(a.x, __ldcs(a.idx + k0 + k));
+    for (int32_t t = lane; t <= nrows; t += 32) S.sp[t] = a.ptr[r0 + t] - k0;
+#pragma unroll
+    for (int32_t j0 = 0; j0 < kCsrW; j0 += 32) {
+        const int32_t j = j0 + lane;
+        if (j < n) {
+            S.sv[j] = __ldcs(a.val + k0 + j);
+            S.sx[j] = ldx(a.x, __ldcs(a.idx + k0 + j));
+        }
     }
-    for (int32_t t = tid; t <= nrows; t += 256) sp[t] = (int32_t)(a.ptr[r0 + t] - k0);
-    __syncthreads();
-    if (tid < nrows && sp[tid + 1] == sp[tid]) csr_put<ADD>(a, r0 + tid, 0.0);  // empty rows
-    const int32_t CT = ((n + 255) >> 8) | 1;
-    const int32_t c0 = tid * CT;
+    __syncwarp();
+    for (int32_t t = lane; t < nrows; t += 32)
+        if (S.sp[t + 1] == S.sp[t]) csr_put<ADD>(a, r0 + t, 0.0);  // empty rows
+    const int32_t CT = ((n + 31) >> 5) | 1;
+    const int32_t c0 = lane * CT;
     const int32_t c1 = c0 + CT < n ? c0 + CT : n;
     double s = 0.0, head = 0.0;
-    int32_t head_row = -1, row = 0, owned_tail = -1;
+    int32_t head_row = -1, owned_tail = -1;
     if (c0 < c1) {
         int32_t lo = 0, hi = nrows - 1;
         while (lo < hi) {  // the row holding nonzero c0
             const int32_t mid = (lo + hi + 1) >> 1;
-            if (sp[mid] <= c0) lo = mid;
+            if (S.sp[mid] <= c0) lo = mid;
             else hi = mid - 1;
         }
-        row = lo;
-        int32_t end = sp[row + 1];
-        bool own = sp[row] == c0;
+        int32_t row = lo;
+        int32_t end = S.sp[row + 1];
+        bool own = S.sp[row] == c0;
         for (int32_t k = c0; k < c1; ++k) {
             if (k == end) {
                 if (own) csr_put<ADD>(a, r0 + row, s);
@@ -189,30 +189,30 @@ __device__ __forceinline__ void csr_unit(const CsrArgs& a, int32_t u, double* sm
                 own = true;
                 do {
                     ++row;
-                    end = sp[row + 1];
+                    end = S.sp[row + 1];
                 } while (end == k);
             }
-            s = fma(sv[k], sx[k], s);
+            s = fma(S.sv[k], S.sx[k], s);
         }
         if (end == c1) {  // the current segment closes at the chunk end
             if (own) csr_put<ADD>(a, r0 + row, s);
             else { head = s; head_row = row; }
         } else if (own) {
-            owned_tail = row;  // continues into later chunks
+            owned_tail = row;  // continues into later lanes
         } else {
             head = s;  // the whole chunk lies inside a row begun earlier
             head_row = row;
         }
     }
-    hv[tid] = head;
-    hr[tid] = head_row;
-    __syncthreads();
+    S.hv[lane] = head;
+    S.hr[lane] = head_row;
+    __syncwarp();
     if (owned_tail >= 0) {
         double acc = s;
-        for (int t2 = tid + 1; t2 < 256 && hr[t2] == owned_tail; ++t2) acc += hv[t2];
+        for (int t2 = lane + 1; t2 < 32 && S.hr[t2] == owned_tail; ++t2) acc += S.hv[t2];
         csr_put<ADD>(a, r0 + owned_tail, acc);
     }
-    __syncthreads();
+    __syncwarp();
 }
 
 // ------------------------------------------------------------------- ELL
