@@ -225,6 +225,26 @@ SPMV_API int spmv_batch_run_separate(spmv_batch* b, const double* const* xs_host
 
 SPMV_API void spmv_batch_free(spmv_batch* b);
 
+/* ------------------------------------------------ allocation-free product */
+
+/* y = A x straight from a caller's device CSR (no handle), allocating no
+ * device memory at all.  For callers that cannot call cudaMalloc when they
+ * need the product: code running while a stream is captured into a CUDA
+ * graph, code under an allocator that owns every device byte, or paths that
+ * must not enter the allocator.  The paper has no counterpart: it is an
+ * interface of this library, computing the same y as spmv_run.
+ *  - csr, x, y: device arrays owned by the caller, layout as for spmv_convert;
+ *    the CSR is not validated (pass one that spmv_convert accepts).
+ *  - Scratch: a static device array of this library (6 MiB, held by every
+ *    GPU that loads the library until the process exits); at most
+ *    536,870,912 nonzeros, SPMV_ERR_TOO_LARGE beyond.
+ *  - The first call on each device looks up that array's device address;
+ *    make the first call on a device before any stream capture.
+ *  - All calls share the one array and keep nothing between calls; calls
+ *    whose kernels overlap on the GPU (different streams, no ordering) race.
+ *  - Asynchronous on `stream`; two kernel launches. */
+SPMV_API int spmv_csr_run_noalloc(const spmv_csr* csr, const double* x, double* y, cudaStream_t stream);
+
 /* --------------------------------------------------------- fault testing */
 
 /* Make the k-th device allocation from now fail with SPMV_ERR_ALLOC

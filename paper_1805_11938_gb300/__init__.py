@@ -26,7 +26,7 @@ __all__ = [
     "SpmvError", "DeviceCSR", "Handle", "Model", "Batch", "spmv_convert", "spmv_run", "spmv_to_csr",
     "spmv_features", "spmv_select", "spmv_select_async", "spmv_mlp_scale", "spmv_mlp_loss_grad", "spmv_mlp_adam",
     "spmv_mlp_train", "spmv_mlp_forward", "spmv_batch_build", "spmv_batch_run", "spmv_batch_run_separate",
-    "spmv_debug_fail_alloc", "lib",
+    "spmv_csr_run_noalloc", "spmv_debug_fail_alloc", "lib",
 ]
 
 
@@ -310,6 +310,15 @@ def spmv_batch_run(b: Batch, xs, ys, stream=None):
 
 def spmv_batch_run_separate(b: Batch, xs, ys, stream=None):
     b.run_separate(xs, ys, stream)
+
+
+def spmv_csr_run_noalloc(csr: DeviceCSR, x, y=None, stream=None):
+    """y = A x from the caller's CSR with no device allocation (see include/spmv.h)."""
+    torch = _torch()
+    if y is None:
+        y = torch.empty(csr.m, dtype=torch.float64, device=x.device)
+    check(lib().spmv_csr_run_noalloc(ctypes.byref(csr.c), _vp(x), _vp(y), _stream(stream)), "spmv_csr_run_noalloc")
+    return y
 
 
 def spmv_debug_fail_alloc(k: int) -> None:

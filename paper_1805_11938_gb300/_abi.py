@@ -79,6 +79,7 @@ _SIGS = {
     "spmv_batch_run": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     "spmv_batch_run_separate": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     "spmv_batch_free": (None, [_VP]),
+    "spmv_csr_run_noalloc": (ctypes.c_int, [ctypes.POINTER(spmv_csr), _VP, _VP, _VP]),
     "spmv_debug_fail_alloc": (None, [_I32]),
 }
 EXPORTED = tuple(_SIGS)
