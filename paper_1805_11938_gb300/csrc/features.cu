@@ -40,26 +40,27 @@ constexpr int kSpread = 16;
 // parameter offsets inside the flat vector
 constexpr int oW1 = 0, oB1 = 1024, oW2 = 1088, oB2 = 5184, oW3 = 5248, oB3 = 5568, kNP = 5573;
 
-struct FeatPart {
+struct FeatStats {  // one CTA's partial statistics of the sampled rows
     unsigned long long sum_len, sum_sq, spread_sum, spread_cnt;
     int min_len, max_len, band;
     unsigned empty, longc;
-    unsigned hist[kLenCap + 1];
 };
 
-__device__ __forceinline__ double feat_transform(int j, double f) {
-    if (j == 0 || j == 1 || j == 3 || j == 4 || j == 5 || j == 6 || j == 11 || j == 12) return log2(1.0 + f);
-    if (j == 2) return -log2(fmax(f, 0x1.0p-60));
+// Transform and min-max scaling of one feature.  FP32 on purpose: this GPU's
+// FP64 pipe makes double log2/division/sqrt several microseconds slower, and
+// the features are float32 values to begin with.
+__device__ __forceinline__ float feat_transform(int j, float f) {
+    if (j == 0 || j == 1 || j == 3 || j == 4 || j == 5 || j == 6 || j == 11 || j == 12) return log2f(1.0f + f);
+    if (j == 2) return -log2f(fmaxf(f, 0x1.0p-60f));
     return f;
 }
 
 __device__ __forceinline__ float feat_scale(int j, float f, const float* lo, const float* hi) {
-    const double t = feat_transform(j, (double)f);
-    const double span = (double)hi[j] - (double)lo[j];
-    if (!(span > 0.0)) return 0.0f;
-    double x = (t - (double)lo[j]) / span;
-    x = x < 0.0 ? 0.0 : (x > 1.0 ? 1.0 : x);
-    return (float)x;
+    const float t = feat_transform(j, f);
+    const float span = hi[j] - lo[j];
+    if (!(span > 0.0f)) return 0.0f;
+    const float x = (t - lo[j]) / span;
+    return x < 0.0f ? 0.0f : (x > 1.0f ? 1.0f : x);
 }
 
 // 16 -> 64 -> 64 -> 5 forward for one sample by the first 64 threads of a block.
@@ -91,20 +92,23 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
                float* __restrict__ feat_out, const float* __restrict__ model_params, const float* __restrict__ lo,
                const float* __restrict__ hi, int32_t* __restrict__ fmt_out, float* __restrict__ logits_out) {
     cg::cluster_group cluster = cg::this_cluster();
-    __shared__ FeatPart part;
+    const unsigned rank = cluster.block_rank();
+    __shared__ unsigned hist[kLenCap + 1];                // this CTA's length histogram
+    __shared__ FeatStats parts[kFeatCtas];                // in CTA 0: every CTA's statistics
+    __shared__ unsigned hists[kFeatCtas * (kLenCap + 1)]; // in CTA 0: every CTA's histogram
     __shared__ unsigned long long red_u[32][4];
     __shared__ int red_i[32][3];
     __shared__ unsigned red_c[32][2];
-    const int tid = threadIdx.x;
-    for (int b = tid; b <= kLenCap; b += kFeatThreads) part.hist[b] = 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int b = tid; b <= kLenCap; b += kFeatThreads) hist[b] = 0;
     __syncthreads();
 
+    // ---- phase 1: every CTA reduces its share of the sampled rows
     const int64_t S = m < kSample ? m : kSample;
     unsigned long long sl = 0, sq = 0, ssum = 0, scnt = 0;
     int mn = 0x7fffffff, mx = 0, band = 0;
     unsigned emp = 0, lng = 0;
-    const int64_t gt = (int64_t)cluster.block_rank() * kFeatThreads + tid;
-    for (int64_t k = gt; k < S; k += (int64_t)kFeatCtas * kFeatThreads) {
+    for (int64_t k = (int64_t)rank * kFeatThreads + tid; k < S; k += (int64_t)kFeatCtas * kFeatThreads) {
         const int64_t i = (k * (int64_t)m) / S;
         const int32_t p0 = ptr[i];
         const int32_t len = ptr[i + 1] - p0;
@@ -116,9 +120,8 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         lng += len >= 32;
         {  // one shared atomic per distinct bin in the warp
             const int bin = len < kLenCap ? len : kLenCap;
-            const unsigned act = __activemask();
-            const unsigned peers = __match_any_sync(act, bin);
-            if ((threadIdx.x & 31) == (__ffs(peers) - 1)) atomicAdd(&part.hist[bin], (unsigned)__popc(peers));
+            const unsigned peers = __match_any_sync(__activemask(), bin);
+            if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
         }
         const int ne = len < kSpread ? len : kSpread;
         int32_t c[kSpread];  // all index loads of the row in flight at once
@@ -133,7 +136,6 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         }
         scnt += (unsigned long long)ne;
     }
-    // block reduction (warp shuffles, then warp 0)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sl += __shfl_xor_sync(dev::kFull, sl, o);
@@ -146,171 +148,163 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         emp += __shfl_xor_sync(dev::kFull, emp, o);
         lng += __shfl_xor_sync(dev::kFull, lng, o);
     }
-    const int w = tid >> 5, l = tid & 31;
-    if (l == 0) {
-        red_u[w][0] = sl; red_u[w][1] = sq; red_u[w][2] = ssum; red_u[w][3] = scnt;
-        red_i[w][0] = mn; red_i[w][1] = mx; red_i[w][2] = band;
-        red_c[w][0] = emp; red_c[w][1] = lng;
+    if (lane == 0) {
+        red_u[warp][0] = sl; red_u[warp][1] = sq; red_u[warp][2] = ssum; red_u[warp][3] = scnt;
+        red_i[warp][0] = mn; red_i[warp][1] = mx; red_i[warp][2] = band;
+        red_c[warp][0] = emp; red_c[warp][1] = lng;
+    }
+    __syncthreads();
+    // push this CTA's partial into CTA 0's shared memory; one cluster barrier publishes them
+    if (tid == 0) {
+        FeatStats p;
+        p.sum_len = p.sum_sq = p.spread_sum = p.spread_cnt = 0;
+        p.min_len = 0x7fffffff; p.max_len = 0; p.band = 0; p.empty = 0; p.longc = 0;
+        for (int q = 0; q < 32; ++q) {
+            p.sum_len += red_u[q][0]; p.sum_sq += red_u[q][1]; p.spread_sum += red_u[q][2]; p.spread_cnt += red_u[q][3];
+            p.min_len = min(p.min_len, red_i[q][0]); p.max_len = max(p.max_len, red_i[q][1]); p.band = max(p.band, red_i[q][2]);
+            p.empty += red_c[q][0]; p.longc += red_c[q][1];
+        }
+        *cluster.map_shared_rank(&parts[rank], 0) = p;
+    }
+    unsigned* h0 = cluster.map_shared_rank(hists, 0);
+    for (int b = tid; b <= kLenCap; b += kFeatThreads) h0[rank * (kLenCap + 1) + b] = hist[b];
+    cluster.sync();
+    if (rank != 0) return;  // CTA 0 holds everything now
+
+    // ---- phase 2 (CTA 0): combine, features, optional selection
+    __shared__ unsigned ck[kLenCap + 2];
+    __shared__ unsigned wsum[32];
+    __shared__ unsigned long long wred[32][3];
+    __shared__ FeatStats tot;
+    __shared__ float fs[16], xs[16], h1[64], h2[64], z[5];
+    __shared__ int Ksh;
+    __shared__ unsigned long long widths, upto_k, capped_sum;
+    if (tid == 0) {
+        FeatStats t = parts[0];
+        for (int r = 1; r < kFeatCtas; ++r) {
+            const FeatStats& q = parts[r];
+            t.sum_len += q.sum_len; t.sum_sq += q.sum_sq; t.spread_sum += q.spread_sum; t.spread_cnt += q.spread_cnt;
+            t.min_len = min(t.min_len, q.min_len); t.max_len = max(t.max_len, q.max_len); t.band = max(t.band, q.band);
+            t.empty += q.empty; t.longc += q.longc;
+        }
+        tot = t;
+    }
+    // c_k = #{len >= k} for k <= 512: suffix sums of the capped histogram (warp shuffles + warp totals)
+    unsigned v = 0;
+    if (tid <= kLenCap) {
+#pragma unroll
+        for (int r = 0; r < kFeatCtas; ++r) v += hists[r * (kLenCap + 1) + tid];
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned u = __shfl_down_sync(dev::kFull, v, d);
+        if (lane + d < 32) v += u;
+    }
+    if (lane == 0) wsum[warp] = v;
+    __syncthreads();
+    {
+        unsigned later = 0;
+        for (int q = warp + 1; q <= kLenCap / 32; ++q) later += wsum[q];
+        if (tid <= kLenCap) ck[tid] = v + later;
+    }
+    __syncthreads();
+    const unsigned cnt = (unsigned)S;
+    const unsigned need = (cnt + 2) / 3;
+    // K = #{k in [1, 512] : c_k >= need}; SELL widths = sum_k ceil(c_k / 32); sum_k c_k = sum min(len, 512)
+    unsigned long long okK = 0, wpart = 0, cpart = 0;
+    if (tid >= 1 && tid <= kLenCap) {
+        okK = ck[tid] >= need;
+        wpart = (ck[tid] + 31) / 32;
+        cpart = ck[tid];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        okK += __shfl_xor_sync(dev::kFull, okK, o);
+        wpart += __shfl_xor_sync(dev::kFull, wpart, o);
+        cpart += __shfl_xor_sync(dev::kFull, cpart, o);
+    }
+    if (lane == 0) {
+        wred[warp][0] = okK;
+        wred[warp][1] = wpart;
+        wred[warp][2] = cpart;
     }
     __syncthreads();
     if (tid == 0) {
-        FeatPart& p = part;
-        p.sum_len = p.sum_sq = p.spread_sum = p.spread_cnt = 0;
-        p.min_len = 0x7fffffff; p.max_len = 0; p.band = 0; p.empty = 0; p.longc = 0;
-        for (int i = 0; i < 32; ++i) {
-            p.sum_len += red_u[i][0]; p.sum_sq += red_u[i][1]; p.spread_sum += red_u[i][2]; p.spread_cnt += red_u[i][3];
-            p.min_len = min(p.min_len, red_i[i][0]); p.max_len = max(p.max_len, red_i[i][1]); p.band = max(p.band, red_i[i][2]);
-            p.empty += red_c[i][0]; p.longc += red_c[i][1];
+        unsigned long long a0 = 0, a1 = 0, a2 = 0;
+        for (int q = 0; q <= kLenCap / 32; ++q) {
+            a0 += wred[q][0];
+            a1 += wred[q][1];
+            a2 += wred[q][2];
         }
+        Ksh = (int)a0;
+        widths = a1;
+        capped_sum = a2;
     }
-    cluster.sync();
-
-    if (cluster.block_rank() == 0) {
-        __shared__ unsigned hist[kLenCap + 1];
-        __shared__ unsigned ck[kLenCap + 2];
-        __shared__ FeatPart tot;
-        __shared__ float fs[16], xs[16], h1[64], h2[64], z[5];
-        __shared__ int Ksh;
-        __shared__ unsigned long long widths;
-        __shared__ unsigned long long upto_k;
-        __shared__ unsigned long long capped_sum;
-        __shared__ FeatPart parts[kFeatCtas];
-        if (tid < kFeatCtas) {  // one thread per cluster rank reads that rank's partial
-            const FeatPart* q = cluster.map_shared_rank(&part, (int)tid);
-            parts[tid].sum_len = q->sum_len; parts[tid].sum_sq = q->sum_sq;
-            parts[tid].spread_sum = q->spread_sum; parts[tid].spread_cnt = q->spread_cnt;
-            parts[tid].min_len = q->min_len; parts[tid].max_len = q->max_len; parts[tid].band = q->band;
-            parts[tid].empty = q->empty; parts[tid].longc = q->longc;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            tot.sum_len = tot.sum_sq = tot.spread_sum = tot.spread_cnt = 0;
-            tot.min_len = 0x7fffffff; tot.max_len = 0; tot.band = 0; tot.empty = 0; tot.longc = 0;
-            for (int r = 0; r < kFeatCtas; ++r) {
-                const FeatPart* q = &parts[r];
-                tot.sum_len += q->sum_len; tot.sum_sq += q->sum_sq;
-                tot.spread_sum += q->spread_sum; tot.spread_cnt += q->spread_cnt;
-                tot.min_len = min(tot.min_len, q->min_len); tot.max_len = max(tot.max_len, q->max_len);
-                tot.band = max(tot.band, q->band); tot.empty += q->empty; tot.longc += q->longc;
-            }
-            Ksh = 0; widths = 0; upto_k = 0; capped_sum = 0;
-        }
-        for (int b = tid; b <= kLenCap; b += kFeatThreads) {
-            unsigned s = 0;
-            for (int r = 0; r < kFeatCtas; ++r) s += cluster.map_shared_rank(&part, r)->hist[b];
-            hist[b] = s;
-        }
-        __syncthreads();
-        // c_k = #{len >= k}: parallel suffix sums of the capped histogram
-        for (int k = tid; k <= kLenCap; k += kFeatThreads) ck[k] = hist[k];
-        __syncthreads();
-        for (int d = 1; d <= kLenCap; d <<= 1) {
-            unsigned v = 0;
-            if (tid <= kLenCap && tid + d <= kLenCap) v = ck[tid + d];
-            __syncthreads();
-            if (tid <= kLenCap) ck[tid] += v;
-            __syncthreads();
-        }
-        const unsigned cnt = (unsigned)S;
-        const unsigned need = (cnt + 2) / 3;
-        // K = #{k in [1, 512] : c_k >= need}; SELL widths = sum_k ceil(c_k / 32);
-        // capped = sum_k c_k = sum min(len, 512): warp shuffles, then one pass over the warps
-        __shared__ unsigned long long wred[32][3];
-        unsigned long long okK = 0, wpart = 0, cpart = 0;
-        if (tid >= 1 && tid <= kLenCap) {
-            okK = ck[tid] >= need;
-            wpart = (ck[tid] + 31) / 32;
-            cpart = ck[tid];
-        }
+    __syncthreads();
+    // sum_{k<=K} c_k = sum min(len, K)
+    unsigned long long up = (tid >= 1 && tid <= Ksh) ? ck[tid] : 0ull;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            okK += __shfl_xor_sync(dev::kFull, okK, o);
-            wpart += __shfl_xor_sync(dev::kFull, wpart, o);
-            cpart += __shfl_xor_sync(dev::kFull, cpart, o);
-        }
-        if ((tid & 31) == 0) {
-            wred[tid >> 5][0] = okK;
-            wred[tid >> 5][1] = wpart;
-            wred[tid >> 5][2] = cpart;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long a0 = 0, a1 = 0, a2 = 0;
-            for (int q = 0; q < kLenCap / 32 + 1; ++q) {
-                a0 += wred[q][0];
-                a1 += wred[q][1];
-                a2 += wred[q][2];
-            }
-            Ksh = (int)a0;
-            widths = a1;
-            capped_sum = a2;
-        }
-        __syncthreads();
-        // sum_{k<=K} c_k = sum min(len, K), by the first warps
-        unsigned long long up = (tid >= 1 && tid <= Ksh) ? ck[tid] : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(dev::kFull, up, o);
-        if ((tid & 31) == 0) wred[tid >> 5][0] = up;
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long a0 = 0;
-            for (int q = 0; q < kLenCap / 32 + 1; ++q) a0 += wred[q][0];
-            upto_k = a0;
-        }
-        __syncthreads();
-        if (tid < 16) {  // one lane per feature, FP64
-            const int j = tid;
-            const double L = (double)tot.sum_len;
-            const double mean = L / (double)cnt;
-            const double nnz = (double)ptr[m];
-            double sd = 0.0;
-            if (j == 6 || j == 7) {
-                // std = sqrt(cnt * sum_sq - L^2) / cnt in exact 128-bit integer arithmetic
-                const unsigned long long a_lo = (unsigned long long)cnt * tot.sum_sq;
-                const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, tot.sum_sq);
-                const unsigned long long b_lo = tot.sum_len * tot.sum_len;
-                const unsigned long long b_hi = __umul64hi(tot.sum_len, tot.sum_len);
-                const unsigned long long d_lo = a_lo - b_lo;
-                const unsigned long long d_hi = a_hi - b_hi - (a_lo < b_lo ? 1ull : 0ull);
-                sd = sqrt((double)d_hi * 18446744073709551616.0 + (double)d_lo) / (double)cnt;
-            }
-            double f = 0.0;
-            switch (j) {
-                case 0: f = (double)m; break;
-                case 1: f = (double)n; break;
-                case 2: f = nnz / ((double)m * (double)n); break;
-                case 3: f = (double)tot.min_len; break;
-                case 4: f = (double)tot.max_len; break;
-                case 5: f = nnz / (double)m; break;
-                case 6: f = sd; break;
-                case 7: f = tot.sum_len > 0 ? sd / mean : 0.0; break;
-                case 8: f = log2(nnz > 1.0 ? nnz : 1.0); break;
-                case 9: f = tot.max_len > 0 ? mean / (double)tot.max_len : 0.0; break;
-                case 10: f = tot.sum_len > 0 ? (double)(tot.sum_len - upto_k) / L : 0.0; break;
-                case 11: f = tot.spread_cnt > 0 ? (double)tot.spread_sum / (double)tot.spread_cnt : 0.0; break;
-                case 12: f = (double)tot.band; break;
-                case 13: f = (double)tot.empty / (double)cnt; break;
-                case 14: f = (double)tot.longc / (double)cnt; break;
-                default: f = widths > 0 ? (double)capped_sum / (32.0 * (double)widths) : 1.0; break;
-            }
-            fs[j] = (float)f;
-        }
-        __syncthreads();
-        if (feat_out && tid < 16) feat_out[tid] = fs[tid];
-        if (model_params) {
-            if (tid < 16) xs[tid] = feat_scale(tid, fs[tid], lo, hi);
-            __syncthreads();
-            mlp_forward_block(model_params, xs, h1, h2, z);
-            if (tid == 0) {
-                int best = 0;
-                for (int c = 1; c < 5; ++c)
-                    if (z[c] > z[best]) best = c;
-                if (fmt_out) fmt_out[0] = best;
-            }
-            if (logits_out && tid < 5) logits_out[tid] = z[tid];
-        }
+    for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(dev::kFull, up, o);
+    if (lane == 0) wred[warp][0] = up;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long a0 = 0;
+        for (int q = 0; q <= kLenCap / 32; ++q) a0 += wred[q][0];
+        upto_k = a0;
     }
-    cluster.sync();  // keep every CTA's shared memory alive until CTA 0 has read it
+    __syncthreads();
+    if (tid < 16) {  // one lane per feature, FP32 (exact integer parts kept in 64 bits)
+        const int j = tid;
+        const float fc = (float)cnt;
+        const float L = (float)tot.sum_len;
+        const float mean = L / fc;
+        const float nnz = (float)ptr[m];
+        float sd = 0.0f;
+        if (j == 6 || j == 7) {
+            // std = sqrt(cnt * sum_sq - L^2) / cnt, the difference in exact 128-bit integer arithmetic
+            const unsigned long long a_lo = (unsigned long long)cnt * tot.sum_sq;
+            const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, tot.sum_sq);
+            const unsigned long long b_lo = tot.sum_len * tot.sum_len;
+            const unsigned long long b_hi = __umul64hi(tot.sum_len, tot.sum_len);
+            const unsigned long long d_lo = a_lo - b_lo;
+            const unsigned long long d_hi = a_hi - b_hi - (a_lo < b_lo ? 1ull : 0ull);
+            sd = sqrtf((float)d_hi * 18446744073709551616.0f + (float)d_lo) / fc;
+        }
+        float f = 0.0f;
+        switch (j) {
+            case 0: f = (float)m; break;
+            case 1: f = (float)n; break;
+            case 2: f = nnz / ((float)m * (float)n); break;
+            case 3: f = (float)tot.min_len; break;
+            case 4: f = (float)tot.max_len; break;
+            case 5: f = nnz / (float)m; break;
+            case 6: f = sd; break;
+            case 7: f = tot.sum_len > 0 ? sd / mean : 0.0f; break;
+            case 8: f = log2f(nnz > 1.0f ? nnz : 1.0f); break;
+            case 9: f = tot.max_len > 0 ? mean / (float)tot.max_len : 0.0f; break;
+            case 10: f = tot.sum_len > 0 ? (float)(tot.sum_len - upto_k) / L : 0.0f; break;
+            case 11: f = tot.spread_cnt > 0 ? (float)tot.spread_sum / (float)tot.spread_cnt : 0.0f; break;
+            case 12: f = (float)tot.band; break;
+            case 13: f = (float)tot.empty / fc; break;
+            case 14: f = (float)tot.longc / fc; break;
+            default: f = widths > 0 ? (float)capped_sum / (32.0f * (float)widths) : 1.0f; break;
+        }
+        fs[j] = f;
+    }
+    __syncthreads();
+    if (feat_out && tid < 16) feat_out[tid] = fs[tid];
+    if (model_params) {
+        if (tid < 16) xs[tid] = feat_scale(tid, fs[tid], lo, hi);
+        __syncthreads();
+        mlp_forward_block(model_params, xs, h1, h2, z);
+        if (tid == 0) {
+            int best = 0;
+            for (int c = 1; c < 5; ++c)
+                if (z[c] > z[best]) best = c;
+            if (fmt_out) fmt_out[0] = best;
+        }
+        if (logits_out && tid < 5) logits_out[tid] = z[tid];
+    }
 }
 
 static int launch_features(const spmv_csr* c, float* feat, const spmv_model* model, int32_t* fmt, float* logits,
@@ -500,8 +494,8 @@ __global__ void __launch_bounds__(1024) k_mlp_train(float* __restrict__ theta, f
     for (int st = 0; st < steps; ++st) {
         mlp_grad_block(S, X, lab, B);
         const int t = t0 + st + 1;
-        const float c1 = (float)(1.0 - pow((double)b1, (double)t));
-        const float c2 = (float)(1.0 - pow((double)b2, (double)t));
+        const float c1 = 1.0f - powf(b1, (float)t);  // FP32: no FP64 in the training loop
+        const float c2 = 1.0f - powf(b2, (float)t);
         for (int p = threadIdx.x; p < kNP; p += blockDim.x) adam_update(S.th, S.g, m, v, p, lr, b1, b2, eps, c1, c2);
         if (loss_hist && threadIdx.x == 0) loss_hist[st] = S.loss;
         __syncthreads();

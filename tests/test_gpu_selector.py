@@ -155,3 +155,30 @@ def test_select_without_model():
     with pytest.raises(sp.SpmvError) as ei:
         sp.spmv_select(d, None)
     assert ei.value.name == "NO_MODEL"
+
+
+def test_committed_model_on_corpus_matrices():
+    """spmv_select with the shipped model picks, on regenerated corpus matrices, what the
+    oracle's network picks from the features stored when the table was profiled."""
+    import json
+    import os
+
+    data = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1805_11938_gb300", "data")
+    with open(os.path.join(data, "selector_mlp.json")) as f:
+        md = json.load(f)
+    with open(os.path.join(data, "corpus_table.jsonl")) as f:
+        recs = {json.loads(l)["index"]: json.loads(l) for l in f}
+    model = sp.Model.load(os.path.join(data, "selector_mlp.json"))
+    theta = np.array(md["params"], np.float64)
+    lo, hi = np.array(md["lo"], np.float64), np.array(md["hi"], np.float64)
+    small = [i for i in sorted(recs) if recs[i]["nnz"] < 2_000_000][:12]
+    for i in small:
+        a = synth.corpus_matrix(i)
+        d = sp.DeviceCSR.from_host(a)
+        f = sp.spmv_features(d).cpu().numpy()
+        assert np.array_equal(f, np.array(recs[i]["features"], np.float32)), i  # the table's features, bit for bit
+        x = mlp.scale(mlp.transform(f.astype(np.float64)), lo, hi)
+        z, _ = mlp.forward(theta, x[None, :])
+        srt = np.sort(z[0])
+        if srt[-1] - srt[-2] > 1e-3:
+            assert sp.spmv_select(d, model) == int(np.argmax(z[0])), i
