@@ -37,6 +37,8 @@ WORKLOADS = {
     "laplacian_64": "2D 5-point Laplacian on 64 x 64 (n = 4096, nnz = 20224)",
     "stencil27_224": "3D 27-point stencil on 224^3 (n = 11,239,424, nnz = 300,763,000)",
     "graph_2e7": "n = 20,000,000 power-law graph, mean about 12 entries per row, at most 1e5",
+    "batch512": "512 matrices, rows log-uniform in [1e3, 2e5], row lengths in [3, 200] (half uniform, half "
+                "power-law), one persistent launch replayed from a CUDA graph",
 }
 
 
@@ -213,6 +215,132 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def tuning_grid(fmt: int) -> list:
+    """The autotuner's small per-format grid used for the batched workload."""
+    if fmt == 1:
+        return [{"csr5_sigma": 16}, {"csr5_sigma": 32}]
+    if fmt == 3:
+        return [{"sell_C": 32, "sell_sigma": 1024}, {"sell_C": 32, "sell_sigma": -1}, {"sell_C": 64, "sell_sigma": -1}]
+    return [{}]
+
+
+def run_batch(args, rank: int, world: int) -> None:
+    """512 matrices, each in the format the selector picks with autotuned parameters, multiplied by one
+    persistent launch (CUDA graph) against the same products as 512 separate launches (also a graph)."""
+    import torch
+
+    import synth
+    import paper_1805_11938_gb300 as sp
+    from paper_1805_11938_gb300 import autotune
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    sp.lib()
+    model = sp.Model.load(sp.MODEL_PATH)
+    timer = autotune.Timer()
+    n_mat = args.batch_count
+    handles, xs, ys, infos, mats = [], [], [], [], []
+    counts = [0] * 5
+    t0 = time.perf_counter()
+    for j in range(n_mat):
+        a = synth.batch_matrix(j + rank * n_mat)
+        d = sp.DeviceCSR.from_host(a)
+        f = sp.spmv_select(d, model)
+        x = torch.as_tensor(synth.vector(a.n, 900 + j)).cuda()
+        y = torch.empty(a.m, dtype=torch.float64, device="cuda")
+        best = None
+        for p in tuning_grid(f):
+            h = sp.spmv_convert(f, d, p)
+            ms = timer.measure(lambda: sp.spmv_run(h, x, y), warmup=1, n_min=5, n_max=10)["ms"]
+            if best is None or ms < best[0]:
+                best = (ms, h)
+        handles.append(best[1])
+        infos.append(best[1].info())
+        xs.append(x)
+        ys.append(y)
+        counts[f] += 1
+        if j < 8:
+            mats.append((a, j))
+        del d
+    t_setup = time.perf_counter() - t0
+    total_nnz = sum(i["nnz"] for i in infos)
+    total_rows = sum(i["m"] for i in infos)
+    b = sp.Batch(handles)
+    ys2 = [torch.empty_like(y) for y in ys]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, n, warm):
+        for _ in range(warm):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for s0, e0 in evs:
+            flush.zero_()
+            s0.record(stream)
+            fn()
+            e0.record(stream)
+        torch.cuda.synchronize()
+        return [s0.elapsed_time(e0) for s0, e0 in evs]
+
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        t_b = timed(lambda: b.run(xs, ys), args.steps, args.warmup)
+    t_s = timed(lambda: b.run_separate(xs, ys2), args.steps, args.warmup)
+    clocks = clk.summary()
+    same = all(torch.equal(u, v) for u, v in zip(ys, ys2))
+    tb = statistics.mean(t_b)
+    ts = statistics.mean(t_s)
+    total_b = sum(t_b)
+    if dist:
+        t = torch.tensor([total_b], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_b = float(t.item())
+    value = world * 2.0 * total_nnz * args.steps / (total_b * 1e6)
+    ab = sum(algorithmic_bytes(i["fmt"], i) for i in infos)
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peaks = json.load(fh)
+    peak = peaks.get("hbm_gbs") or 6800.0
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_b / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "matrices": n_mat,
+                       "rows": total_rows, "nnz": total_nnz, "formats": dict(zip(FORMATS, counts)),
+                       "l2": "flushed: 256 MiB written before every timed step", "setup_s": t_setup,
+                       "step": "one graph replay of the persistent batched kernel over all matrices"},
+            "roofline": {"bound": "hbm", "achieved": ab / tb / 1e6, "peak": peak, "unit": "GB/s",
+                         "frac": ab / tb / 1e6 / peak, "traffic": None, "kernel": "persistent batched product",
+                         "alg_bytes_per_launch": ab},
+            "batched_ms": tb, "separate_ms": ts, "batched_speedup_over_separate": ts / tb,
+            "separate_gflops": 2.0 * total_nnz / ts / 1e6, "bitwise_equal_to_separate": same,
+            "gpu_launches": args.steps * 2, "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        oks = []
+        for a, j in mats:
+            yv = ys[j].cpu().numpy()
+            xv = xs[j].cpu().numpy()
+            oks.append(bool(np.all(np.abs(yv - oracle.csr_spmv(a, xv)) <= oracle.fp_bound(a, xv))))
+        line["check"] = {"first_8_matrices_within_bound": all(oks)}
+        line["cpu_baseline"] = cpu_oracle_rate(mats[0][0], xs[0].cpu().numpy(), min(args.cpu_seconds, 5.0))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -225,12 +353,16 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--formats", default="0,1,2,3,4")
+    ap.add_argument("--batch-count", type=int, default=512)
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch512":
+        run_batch(args, rank, world)
         return
 
     import torch
