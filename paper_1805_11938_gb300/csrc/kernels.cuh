@@ -60,10 +60,11 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
 // Work is split into warp units (units[u] = {r0, k0, c, nch}; the next unit
 // gives r1 and k1):
 //  * c = -1, several rows (fewer than kCsrW nonzeros, at most kCsrRows rows):
-//    the warp stages values and gathered x[idx] in its shared slice with
+//    the warp stages values and column indices in its shared slice with
 //    coalesced loads, then lane l walks the contiguous chunk
-//    [l*CT, l*CT + CT) (CT odd: conflict-free 8-byte shared accesses) with one
-//    DFMA per nonzero, writing every row that begins and ends in its chunk;
+//    [l*CT, l*CT + CT) (CT odd: conflict-free shared accesses), gathering x
+//    and issuing one DFMA per nonzero, writing every row that begins and ends
+//    in its chunk;
 //    a row begun in an earlier lane leaves its partial in shared memory and
 //    the lane owning the row's start adds those partials in lane order;
 //  * c = -1, one row longer than the unit budget: lanes stride the row with
@@ -71,7 +72,7 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
 //  * c >= 0: chunk c of nch of a row longer than kCsrChunk; partials go to
 //    partial[u] and the last chunk to finish (atomic ticket) adds them in
 //    order.
-constexpr int kCsrW = 224;      // a multi-row unit holds fewer nonzeros than this
+constexpr int kCsrW = 416;      // a multi-row unit holds fewer nonzeros than this
 constexpr int kCsrRows = 64;    // and at most this many rows
 constexpr int kCsrChunk = 2048; // rows longer than this are split into chunks
 
@@ -89,8 +90,8 @@ struct CsrArgs {
 
 struct CsrWarpSmem {
     double sv[kCsrW];
-    double sx[kCsrW];
     double hv[32];
+    int32_t si[kCsrW];
     int32_t sp[kCsrRows + 1];
     int32_t hr[32];
 };
@@ -155,13 +156,12 @@ __device__ __forceinline__ void csr_warp_unit(const CsrArgs& a, int32_t u, CsrWa
         return;
     }
     for (int32_t t = lane; t <= nrows; t += 32) S.sp[t] = a.ptr[r0 + t] - k0;
-#pragma unroll
-    for (int32_t j0 = 0; j0 < kCsrW; j0 += 32) {
-        const int32_t j = j0 + lane;
-        if (j < n) {
-            S.sv[j] = __ldcs(a.val + k0 + j);
-            S.sx[j] = ldx(a.x, __ldcs(a.idx + k0 + j));
-        }
+    const double* __restrict__ vb = a.val + k0;
+    const int32_t* __restrict__ ib = a.idx + k0;
+#pragma unroll 4
+    for (int32_t j = lane; j < n; j += 32) {
+        S.sv[j] = __ldcs(vb + j);
+        S.si[j] = __ldcs(ib + j);
     }
     __syncwarp();
     for (int32_t t = lane; t < nrows; t += 32)
@@ -181,7 +181,9 @@ __device__ __forceinline__ void csr_warp_unit(const CsrArgs& a, int32_t u, CsrWa
         int32_t row = lo;
         int32_t end = S.sp[row + 1];
         bool own = S.sp[row] == c0;
+#pragma unroll 4
         for (int32_t k = c0; k < c1; ++k) {
+            const double xv = ldx(a.x, S.si[k]);
             if (k == end) {
                 if (own) csr_put<ADD>(a, r0 + row, s);
                 else { head = s; head_row = row; }
@@ -192,7 +194,7 @@ __device__ __forceinline__ void csr_warp_unit(const CsrArgs& a, int32_t u, CsrWa
                     end = S.sp[row + 1];
                 } while (end == k);
             }
-            s = fma(S.sv[k], S.sx[k], s);
+            s = fma(S.sv[k], xv, s);
         }
         if (end == c1) {  // the current segment closes at the chunk end
             if (own) csr_put<ADD>(a, r0 + row, s);
