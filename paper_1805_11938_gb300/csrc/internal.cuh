@@ -16,7 +16,7 @@ namespace spmv {
 
 constexpr int kThreads = 256;      // block size of the SpMV kernels
 constexpr int kEllLongRow = 64;    // ELL rows longer than this go to the warp-per-row kernel
-constexpr int kSellUnitWidth = 256;  // SELL slices wider than this are split over several warps
+constexpr int kSellUnitWidth = 64;   // SELL slices wider than this are split over several warps
 constexpr int kCsr5Omega = 32;     // CSR5 tile width = warp width
 
 int set_error(int code, const char* fmt, ...);

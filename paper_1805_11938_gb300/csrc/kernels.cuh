@@ -74,7 +74,7 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
 //    order.
 constexpr int kCsrW = 416;      // a multi-row unit holds fewer nonzeros than this
 constexpr int kCsrRows = 64;    // and at most this many rows
-constexpr int kCsrChunk = 2048; // rows longer than this are split into chunks
+constexpr int kCsrChunk = 1024; // rows longer than this are split into chunks
 
 struct CsrArgs {
     const int4* units;
@@ -141,6 +141,7 @@ __device__ __forceinline__ void csr_warp_unit(const CsrArgs& a, int32_t u, CsrWa
             if (prev == (unsigned)(U.w - 1)) {
                 __threadfence();
                 double acc = 0.0;
+#pragma unroll 8
                 for (int32_t c = 0; c < U.w; ++c) acc += __ldcg(a.partial + first + c);
                 a.counters[first] = 0u;
                 csr_put<ADD>(a, r0, acc);
@@ -316,7 +317,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane
 #pragma unroll
     for (int r = 0; r < R; ++r) lmax = L[r] > lmax ? L[r] : lmax;
     const int32_t jend = j1 < lmax ? j1 : lmax;
-#pragma unroll 4
+#pragma unroll 8
     for (int32_t j = j0; j < jend; ++j) {
         const int64_t o = base + (int64_t)j * C + lane * R;
         if constexpr (R == 1) {
@@ -359,6 +360,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         double t = 0.0;
+#pragma unroll 8
         for (int32_t c = 0; c < nch; ++c) t += __ldcg(a.partial + (int64_t)(first + c) * C + lane * R + r);
         if (p0 + r < a.m) a.y[a.perm[p0 + r]] = t;
     }
@@ -413,6 +415,7 @@ __device__ __forceinline__ void csr5_tile(const Csr5Args& a, int64_t t, int lane
     const int64_t kl = base + (int64_t)lane * a.sigma;
     double cur = 0.0, head = 0.0;
     int j = 0;  // segments of this lane seen so far
+#pragma unroll 8
     for (int r = 0; r < a.sigma; ++r) {
         const int64_t slot = base + (int64_t)r * 32 + lane;
         const bool valid = kl + r < a.nnz;  // false only in the padded last tile
