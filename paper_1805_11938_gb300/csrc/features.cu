@@ -17,6 +17,7 @@
 // partial results through distributed shared memory (no global scratch, no
 // atomics across CTAs) and, for selection, runs the network.
 #include <cooperative_groups.h>
+#include <cuda_pipeline.h>
 
 #include "internal.cuh"
 #include "kernels.cuh"
@@ -63,26 +64,48 @@ __device__ __forceinline__ float feat_scale(int j, float f, const float* lo, con
     return x < 0.0f ? 0.0f : (x > 1.0f ? 1.0f : x);
 }
 
-// 16 -> 64 -> 64 -> 5 forward for one sample by the first 64 threads of a block.
-// xs: 16 floats (shared), h1, h2: 64 floats (shared), z: 5 floats (shared).
-__device__ void mlp_forward_block(const float* __restrict__ th, const float* xs, float* h1, float* h2, float* z) {
-    const int j = threadIdx.x;
-    if (j < 64) {
-        float a = th[oB1 + j];
-        for (int i = 0; i < 16; ++i) a = fmaf(xs[i], th[oW1 + i * 64 + j], a);
-        h1[j] = a > 0.f ? a : 0.f;
+// 16 -> 64 -> 64 -> 5 forward for one sample; th in shared memory.  Four
+// threads share each hidden unit and eight each logit (partial sums joined by
+// shuffles), so no thread runs a 64-long dependent chain.
+__device__ void mlp_forward_block(const float* th, const float* xs, float* h1, float* h2, float* z) {
+    const int t = threadIdx.x;
+    if (t < 256) {
+        const int j = t >> 2, q = t & 3;
+        float a = 0.f;
+#pragma unroll
+        for (int i = q; i < 16; i += 4) a = fmaf(xs[i], th[oW1 + i * 64 + j], a);
+        a += __shfl_xor_sync(dev::kFull, a, 1);
+        a += __shfl_xor_sync(dev::kFull, a, 2);
+        if (q == 0) {
+            a += th[oB1 + j];
+            h1[j] = a > 0.f ? a : 0.f;
+        }
     }
     __syncthreads();
-    if (j < 64) {
-        float a = th[oB2 + j];
-        for (int i = 0; i < 64; ++i) a = fmaf(h1[i], th[oW2 + i * 64 + j], a);
-        h2[j] = a > 0.f ? a : 0.f;
+    if (t < 256) {
+        const int j = t >> 2, q = t & 3;
+        float a = 0.f;
+#pragma unroll
+        for (int i = q; i < 64; i += 4) a = fmaf(h1[i], th[oW2 + i * 64 + j], a);
+        a += __shfl_xor_sync(dev::kFull, a, 1);
+        a += __shfl_xor_sync(dev::kFull, a, 2);
+        if (q == 0) {
+            a += th[oB2 + j];
+            h2[j] = a > 0.f ? a : 0.f;
+        }
     }
     __syncthreads();
-    if (j < 5) {
-        float a = th[oB3 + j];
-        for (int i = 0; i < 64; ++i) a = fmaf(h2[i], th[oW3 + i * 5 + j], a);
-        z[j] = a;
+    if (t < 64) {  // 5 logits x 8 lanes (lanes 40..63 idle)
+        const int c = t >> 3, q = t & 7;
+        float a = 0.f;
+        if (c < 5) {
+#pragma unroll
+            for (int i = q; i < 64; i += 8) a = fmaf(h2[i], th[oW3 + i * 5 + c], a);
+        }
+        a += __shfl_xor_sync(dev::kFull, a, 1);
+        a += __shfl_xor_sync(dev::kFull, a, 2);
+        a += __shfl_xor_sync(dev::kFull, a, 4);
+        if (c < 5 && q == 0) z[c] = a + th[oB3 + c];
     }
     __syncthreads();
 }
@@ -100,6 +123,18 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
     __shared__ int red_i[32][3];
     __shared__ unsigned red_c[32][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // CTA 0 of a selection starts copying the network into shared memory now
+    // (asynchronous copies, waited for just before the network runs).
+    __shared__ __align__(16) float wsm[kNP + 3 + 32];
+    if (model_params && rank == 0) {
+        for (int c = tid; c < kNP / 4; c += kFeatThreads) __pipeline_memcpy_async(wsm + 4 * c, model_params + 4 * c, 16);
+        if (tid < kNP % 4) wsm[(kNP / 4) * 4 + tid] = model_params[(kNP / 4) * 4 + tid];
+        if (tid < 16) {
+            wsm[kNP + 3 + tid] = lo[tid];
+            wsm[kNP + 3 + 16 + tid] = hi[tid];
+        }
+        __pipeline_commit();
+    }
     for (int b = tid; b <= kLenCap; b += kFeatThreads) hist[b] = 0;
     __syncthreads();
 
@@ -294,9 +329,11 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
     __syncthreads();
     if (feat_out && tid < 16) feat_out[tid] = fs[tid];
     if (model_params) {
-        if (tid < 16) xs[tid] = feat_scale(tid, fs[tid], lo, hi);
+        __pipeline_wait_prior(0);
         __syncthreads();
-        mlp_forward_block(model_params, xs, h1, h2, z);
+        if (tid < 16) xs[tid] = feat_scale(tid, fs[tid], wsm + kNP + 3, wsm + kNP + 3 + 16);
+        __syncthreads();
+        mlp_forward_block(wsm, xs, h1, h2, z);
         if (tid == 0) {
             int best = 0;
             for (int c = 1; c < 5; ++c)
