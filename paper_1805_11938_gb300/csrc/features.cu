@@ -138,38 +138,61 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
     for (int b = tid; b <= kLenCap; b += kFeatThreads) hist[b] = 0;
     __syncthreads();
 
-    // ---- phase 1: every CTA reduces its share of the sampled rows
+    // ---- phase 1: every CTA reduces its share of the sampled rows.  A thread
+    // holds at most two sampled rows (8 CTAs x 1024 threads, 16384 samples);
+    // both rows' loads are issued together.  Row of sample k: k*M/S, with
+    // S = 16384 = 2^14 whenever M > S (a shift), else k.
     const int64_t S = m < kSample ? m : kSample;
     unsigned long long sl = 0, sq = 0, ssum = 0, scnt = 0;
     int mn = 0x7fffffff, mx = 0, band = 0;
     unsigned emp = 0, lng = 0;
-    for (int64_t k = (int64_t)rank * kFeatThreads + tid; k < S; k += (int64_t)kFeatCtas * kFeatThreads) {
-        const int64_t i = (k * (int64_t)m) / S;
-        const int32_t p0 = ptr[i];
-        const int32_t len = ptr[i + 1] - p0;
-        sl += (unsigned long long)len;
-        sq += (unsigned long long)len * (unsigned long long)len;
-        mn = min(mn, len);
-        mx = max(mx, len);
-        emp += len == 0;
-        lng += len >= 32;
-        {  // one shared atomic per distinct bin in the warp
-            const int bin = len < kLenCap ? len : kLenCap;
-            const unsigned peers = __match_any_sync(__activemask(), bin);
-            if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
-        }
-        const int ne = len < kSpread ? len : kSpread;
-        int32_t c[kSpread];  // all index loads of the row in flight at once
+    {
+        const int64_t kk[2] = {(int64_t)rank * kFeatThreads + tid, (int64_t)rank * kFeatThreads + tid + kFeatCtas * kFeatThreads};
+        int64_t ii[2];
+        int32_t p0[2], p1[2];
 #pragma unroll
-        for (int q = 0; q < kSpread; ++q) c[q] = q < ne ? __ldg(idx + p0 + q) : (int32_t)i;
-#pragma unroll
-        for (int q = 0; q < kSpread; ++q) {
-            const int64_t d = (int64_t)c[q] - i;
-            const int ad = (int)(d < 0 ? -d : d);
-            ssum += (unsigned long long)ad;
-            band = max(band, ad);
+        for (int r = 0; r < 2; ++r) {
+            ii[r] = m > kSample ? ((kk[r] * (int64_t)m) >> 14) : kk[r];
+            const bool on = kk[r] < S;
+            p0[r] = on ? ptr[ii[r]] : 0;
+            p1[r] = on ? ptr[ii[r] + 1] : 0;
         }
-        scnt += (unsigned long long)ne;
+        int32_t c[2][kSpread];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int32_t len = p1[r] - p0[r];
+            const int ne = len < kSpread ? len : kSpread;
+#pragma unroll
+            for (int q = 0; q < kSpread; ++q) c[r][q] = q < ne ? __ldg(idx + p0[r] + q) : (int32_t)ii[r];
+        }
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const bool on = kk[r] < S;
+            const int32_t len = p1[r] - p0[r];
+            if (on) {
+                sl += (unsigned long long)len;
+                sq += (unsigned long long)len * (unsigned long long)len;
+                mn = min(mn, len);
+                mx = max(mx, len);
+                emp += len == 0;
+                lng += len >= 32;
+                scnt += (unsigned long long)(len < kSpread ? len : kSpread);
+#pragma unroll
+                for (int q = 0; q < kSpread; ++q) {
+                    const int64_t d = (int64_t)c[r][q] - ii[r];
+                    const int ad = (int)(d < 0 ? -d : d);
+                    ssum += (unsigned long long)ad;
+                    band = max(band, ad);
+                }
+            }
+            // one shared atomic per distinct bin in the warp
+            const unsigned act = __ballot_sync(dev::kFull, on);
+            if (on) {
+                const int bin = len < kLenCap ? len : kLenCap;
+                const unsigned peers = __match_any_sync(act, bin);
+                if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -189,105 +212,124 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         red_c[warp][0] = emp; red_c[warp][1] = lng;
     }
     __syncthreads();
-    // push this CTA's partial into CTA 0's shared memory; one cluster barrier publishes them
-    if (tid == 0) {
-        FeatStats p;
-        p.sum_len = p.sum_sq = p.spread_sum = p.spread_cnt = 0;
-        p.min_len = 0x7fffffff; p.max_len = 0; p.band = 0; p.empty = 0; p.longc = 0;
-        for (int q = 0; q < 32; ++q) {
-            p.sum_len += red_u[q][0]; p.sum_sq += red_u[q][1]; p.spread_sum += red_u[q][2]; p.spread_cnt += red_u[q][3];
-            p.min_len = min(p.min_len, red_i[q][0]); p.max_len = max(p.max_len, red_i[q][1]); p.band = max(p.band, red_i[q][2]);
-            p.empty += red_c[q][0]; p.longc += red_c[q][1];
+    // push this CTA's partial into CTA 0's shared memory; one cluster barrier publishes them.
+    // Warp 0 combines the 32 warp partials with shuffles.
+    if (warp == 0) {
+        unsigned long long a0 = red_u[lane][0], a1 = red_u[lane][1], a2 = red_u[lane][2], a3 = red_u[lane][3];
+        int i0 = red_i[lane][0], i1 = red_i[lane][1], i2 = red_i[lane][2];
+        unsigned c0 = red_c[lane][0], c1 = red_c[lane][1];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(dev::kFull, a0, o);
+            a1 += __shfl_xor_sync(dev::kFull, a1, o);
+            a2 += __shfl_xor_sync(dev::kFull, a2, o);
+            a3 += __shfl_xor_sync(dev::kFull, a3, o);
+            i0 = min(i0, __shfl_xor_sync(dev::kFull, i0, o));
+            i1 = max(i1, __shfl_xor_sync(dev::kFull, i1, o));
+            i2 = max(i2, __shfl_xor_sync(dev::kFull, i2, o));
+            c0 += __shfl_xor_sync(dev::kFull, c0, o);
+            c1 += __shfl_xor_sync(dev::kFull, c1, o);
         }
-        *cluster.map_shared_rank(&parts[rank], 0) = p;
+        if (lane == 0) {
+            FeatStats p;
+            p.sum_len = a0; p.sum_sq = a1; p.spread_sum = a2; p.spread_cnt = a3;
+            p.min_len = i0; p.max_len = i1; p.band = i2; p.empty = c0; p.longc = c1;
+            *cluster.map_shared_rank(&parts[rank], 0) = p;
+        }
     }
     unsigned* h0 = cluster.map_shared_rank(hists, 0);
     for (int b = tid; b <= kLenCap; b += kFeatThreads) h0[rank * (kLenCap + 1) + b] = hist[b];
     cluster.sync();
     if (rank != 0) return;  // CTA 0 holds everything now
 
-    // ---- phase 2 (CTA 0): combine, features, optional selection
-    __shared__ unsigned ck[kLenCap + 2];
-    __shared__ unsigned wsum[32];
-    __shared__ unsigned long long wred[32][3];
+    // ---- phase 2 (CTA 0): combine, features, optional selection.  The
+    // histogram ranks are summed by 513 threads; the rest runs in warp 0 with
+    // shuffles only (lane l owns bins 17l .. 17l + 16).
+    __shared__ unsigned hsum[kLenCap + 1];
     __shared__ FeatStats tot;
     __shared__ float fs[16], xs[16], h1[64], h2[64], z[5];
-    __shared__ int Ksh;
-    __shared__ unsigned long long widths, upto_k, capped_sum;
-    if (tid == 0) {
-        FeatStats t = parts[0];
-        for (int r = 1; r < kFeatCtas; ++r) {
-            const FeatStats& q = parts[r];
-            t.sum_len += q.sum_len; t.sum_sq += q.sum_sq; t.spread_sum += q.spread_sum; t.spread_cnt += q.spread_cnt;
-            t.min_len = min(t.min_len, q.min_len); t.max_len = max(t.max_len, q.max_len); t.band = max(t.band, q.band);
-            t.empty += q.empty; t.longc += q.longc;
-        }
-        tot = t;
-    }
-    // c_k = #{len >= k} for k <= 512: suffix sums of the capped histogram (warp shuffles + warp totals)
-    unsigned v = 0;
     if (tid <= kLenCap) {
+        unsigned v = 0;
 #pragma unroll
         for (int r = 0; r < kFeatCtas; ++r) v += hists[r * (kLenCap + 1) + tid];
+        hsum[tid] = v;
     }
+    if (warp == 0) {  // combine the eight CTA partials (lanes 0..7) with shuffles
+        const int r = lane < kFeatCtas ? lane : 0;
+        const bool on = lane < kFeatCtas;
+        unsigned long long a0 = on ? parts[r].sum_len : 0, a1 = on ? parts[r].sum_sq : 0;
+        unsigned long long a2 = on ? parts[r].spread_sum : 0, a3 = on ? parts[r].spread_cnt : 0;
+        int i0 = on ? parts[r].min_len : 0x7fffffff, i1 = on ? parts[r].max_len : 0, i2 = on ? parts[r].band : 0;
+        unsigned c0 = on ? parts[r].empty : 0, c1 = on ? parts[r].longc : 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const unsigned u = __shfl_down_sync(dev::kFull, v, d);
-        if (lane + d < 32) v += u;
-    }
-    if (lane == 0) wsum[warp] = v;
-    __syncthreads();
-    {
-        unsigned later = 0;
-        for (int q = warp + 1; q <= kLenCap / 32; ++q) later += wsum[q];
-        if (tid <= kLenCap) ck[tid] = v + later;
+        for (int o = 4; o > 0; o >>= 1) {
+            a0 += __shfl_xor_sync(dev::kFull, a0, o);
+            a1 += __shfl_xor_sync(dev::kFull, a1, o);
+            a2 += __shfl_xor_sync(dev::kFull, a2, o);
+            a3 += __shfl_xor_sync(dev::kFull, a3, o);
+            i0 = min(i0, __shfl_xor_sync(dev::kFull, i0, o));
+            i1 = max(i1, __shfl_xor_sync(dev::kFull, i1, o));
+            i2 = max(i2, __shfl_xor_sync(dev::kFull, i2, o));
+            c0 += __shfl_xor_sync(dev::kFull, c0, o);
+            c1 += __shfl_xor_sync(dev::kFull, c1, o);
+        }
+        if (lane == 0) {
+            tot.sum_len = a0; tot.sum_sq = a1; tot.spread_sum = a2; tot.spread_cnt = a3;
+            tot.min_len = i0; tot.max_len = i1; tot.band = i2; tot.empty = c0; tot.longc = c1;
+        }
     }
     __syncthreads();
     const unsigned cnt = (unsigned)S;
-    const unsigned need = (cnt + 2) / 3;
-    // K = #{k in [1, 512] : c_k >= need}; SELL widths = sum_k ceil(c_k / 32); sum_k c_k = sum min(len, 512)
-    unsigned long long okK = 0, wpart = 0, cpart = 0;
-    if (tid >= 1 && tid <= kLenCap) {
-        okK = ck[tid] >= need;
-        wpart = (ck[tid] + 31) / 32;
-        cpart = ck[tid];
-    }
+    unsigned long long upto_k = 0, widths = 0, capped_sum = 0;
+    if (warp == 0) {
+        // c_b = #{len >= b}: suffix sums over the bins (in-lane, then over the lanes)
+        constexpr int PB = 17;  // bins per lane: 32 * 17 = 544 >= 513
+        unsigned c[PB];
+        unsigned run = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        okK += __shfl_xor_sync(dev::kFull, okK, o);
-        wpart += __shfl_xor_sync(dev::kFull, wpart, o);
-        cpart += __shfl_xor_sync(dev::kFull, cpart, o);
-    }
-    if (lane == 0) {
-        wred[warp][0] = okK;
-        wred[warp][1] = wpart;
-        wred[warp][2] = cpart;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long a0 = 0, a1 = 0, a2 = 0;
-        for (int q = 0; q <= kLenCap / 32; ++q) {
-            a0 += wred[q][0];
-            a1 += wred[q][1];
-            a2 += wred[q][2];
+        for (int j = PB - 1; j >= 0; --j) {
+            const int bb = lane * PB + j;
+            run += bb <= kLenCap ? hsum[bb] : 0u;
+            c[j] = run;  // in-lane suffix
         }
-        Ksh = (int)a0;
-        widths = a1;
-        capped_sum = a2;
-    }
-    __syncthreads();
-    // sum_{k<=K} c_k = sum min(len, K)
-    unsigned long long up = (tid >= 1 && tid <= Ksh) ? ck[tid] : 0ull;
+        unsigned later = run;  // this lane's total, then the totals of later lanes
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(dev::kFull, up, o);
-    if (lane == 0) wred[warp][0] = up;
-    __syncthreads();
-    if (tid == 0) {
-        unsigned long long a0 = 0;
-        for (int q = 0; q <= kLenCap / 32; ++q) a0 += wred[q][0];
-        upto_k = a0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned u = __shfl_down_sync(dev::kFull, later, d);
+            if (lane + d < 32) later += u;
+        }
+        later -= run;
+        const unsigned need = (cnt + 2) / 3;
+        unsigned long long k_ok = 0, wpart = 0, cpart = 0;
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+            const int bb = lane * PB + j;
+            c[j] += later;
+            if (bb >= 1 && bb <= kLenCap) {
+                k_ok += c[j] >= need;
+                wpart += (c[j] + 31) / 32;
+                cpart += c[j];
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            k_ok += __shfl_xor_sync(dev::kFull, k_ok, o);
+            wpart += __shfl_xor_sync(dev::kFull, wpart, o);
+            cpart += __shfl_xor_sync(dev::kFull, cpart, o);
+        }
+        const int K = (int)k_ok;  // c_b is non-increasing, so the bins >= need are 1..K
+        unsigned long long up = 0;
+#pragma unroll
+        for (int j = 0; j < PB; ++j) {
+            const int bb = lane * PB + j;
+            if (bb >= 1 && bb <= K) up += c[j];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(dev::kFull, up, o);
+        upto_k = up;  // sum min(len, K)
+        widths = wpart;
+        capped_sum = cpart;
     }
-    __syncthreads();
     if (tid < 16) {  // one lane per feature, FP32 (exact integer parts kept in 64 bits)
         const int j = tid;
         const float fc = (float)cnt;
