@@ -64,7 +64,7 @@ def algorithmic_bytes(fmt: int, info: dict) -> int:
     aux = info["aux"]
     if fmt == 0:  # CSR: row pointers
         return base + 4 * (m + 1)
-    if fmt == 1:  # CSR5: per tile 32 flag words, tile_ptr, empty_ptr, the head row's pointer, carry
+    if fmt == 1:  # CSR5: per tile 32 flag words, tile_ptr, empty_ptr, the head row's pointer, join slots
         return base + aux[0] * (128 + 4 + 8 + 4 + 16)
     if fmt == 2:  # ELL: row_len
         return base + 4 * m
@@ -77,7 +77,7 @@ def algorithmic_bytes(fmt: int, info: dict) -> int:
 def launches_per_run(fmt: int, info: dict) -> int:
     aux = info["aux"]
     if fmt == 1:
-        return (1 if aux[0] > 0 else 0) + (1 if max(aux[0], aux[2]) > 0 else 0)
+        return 1 if (aux[0] > 0 or aux[2] > 0) else 0
     if fmt == 4:
         return 1 + (1 if aux[1] > 0 else 0)
     return 1
@@ -250,7 +250,7 @@ def run_batch(args, rank: int, world: int) -> None:
     for j in range(n_mat):
         a = synth.batch_matrix(j + rank * n_mat)
         d = sp.DeviceCSR.from_host(a)
-        f = sp.spmv_select(d, model)
+        f = sp.spmv_select(d, model) if args.batch_format < 0 else args.batch_format
         x = torch.as_tensor(synth.vector(a.n, 900 + j)).cuda()
         y = torch.empty(a.m, dtype=torch.float64, device="cuda")
         best = None
@@ -316,6 +316,7 @@ def run_batch(args, rank: int, world: int) -> None:
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "matrices": n_mat,
                        "rows": total_rows, "nnz": total_nnz, "formats": dict(zip(FORMATS, counts)),
+                       "format_choice": "selector" if args.batch_format < 0 else "fixed",
                        "l2": "flushed: 256 MiB written before every timed step", "setup_s": t_setup,
                        "step": "one graph replay of the persistent batched kernel over all matrices"},
             "roofline": {"bound": "hbm", "achieved": ab / tb / 1e6, "peak": peak, "unit": "GB/s",
@@ -354,6 +355,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--formats", default="0,1,2,3,4")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-format", type=int, default=-1, help="batch512: one format for every matrix (-1: selector)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))

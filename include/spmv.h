@@ -131,7 +131,9 @@ SPMV_API int spmv_convert(spmv_fmt fmt, const spmv_csr* csr, const spmv_params* 
 
 /* y = A x (Sec. II-A), y overwritten (beta = 0).  x holds N doubles and y M
  * doubles, both device memory.  Asynchronous on `stream`; no host sync.
- * Launches the format's kernels (one to three launches). */
+ * Launches the format's kernels (one or two launches).  Runs of one handle
+ * must not overlap on the GPU (they share the handle's small scratch for
+ * rows split across warps); runs of different handles may. */
 SPMV_API int spmv_run(const spmv_handle* h, const double* x, double* y, cudaStream_t stream);
 
 /* Write A back as CSR (ptr[M+1], idx[nnz], val[nnz], device, caller-owned).

@@ -1,6 +1,6 @@
 // Batched SpMV: many independent products y_b = A_b x_b, each matrix in its
 // own format, in one persistent launch (plus a second one for the passes that
-// must follow the first: CSR5 carry calibration and the HYB COO tail).
+// must follow the first: the HYB COO tail).
 //
 // The work list is built once on the host from the handles' unit counts:
 // task = {matrix, kind, index}.  A grid of (SMs x resident blocks) 256-thread
@@ -23,16 +23,14 @@ enum TaskKind : int32_t {
     T_ELL = 2,       // 512 ELL rows
     T_ELL_LONG = 3,  // one long ELL row
     T_SELL = 4,      // 8 SELL units (warp each)
-    T_CSR5_CAL = 5,  // 256 tiles of calibration / empty rows
+    T_CSR5_ZERO = 5, // 256 empty rows of a CSR5 matrix without nonzeros
     T_HYB_TAIL = 6   // 8 HYB tail warp units, adding into y
 };
 
 struct MatDesc {
     int32_t fmt, sell_r;
-    int32_t n_zero;
     int32_t csr_units;
     int32_t ell_nb;
-    const int32_t* zero_rows;
     const int32_t* long_rows;
     dev::CsrArgs csr;   // CSR, or the HYB tail (ADD)
     dev::Csr5Args csr5;
@@ -89,11 +87,11 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
                 if (tile < a.ntiles) dev::csr5_tile(a, tile, lane);
                 break;
             }
-            case T_CSR5_CAL: {
+            case T_CSR5_ZERO: {
                 dev::Csr5Args a = md.csr5;
                 a.x = x;
                 a.y = y;
-                dev::csr5_calibrate(a, (int64_t)t.z * 256 + threadIdx.x, md.zero_rows, md.n_zero);
+                dev::csr5_zero_all(a, (int64_t)t.z * 256 + threadIdx.x);
                 break;
             }
             case T_ELL: {
@@ -163,6 +161,8 @@ struct spmv_batch {
 
 namespace spmv {
 
+dev::Csr5Args csr5_args(const spmv_handle* h, const double* x, double* y);
+
 static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, std::vector<int4>& t2, int32_t b) {
     memset(&d, 0, sizeof d);
     d.fmt = h->fmt;
@@ -174,14 +174,12 @@ static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, s
             for (int64_t g = 0; g < ceil_div(h->cu.n, 8); ++g) t1.push_back(make_int4(b, T_CSR, (int32_t)g, 0));
             break;
         case SPMV_CSR5: {
-            d.csr5 = dev::Csr5Args{h->ptr, h->tile_ptr, h->flags, h->tile_idx, h->tile_val, h->empty_ptr, h->empty_rows,
-                                   h->carry, h->nnz, h->ntiles, h->csr5_sigma, nullptr, nullptr};
-            d.zero_rows = h->zero_rows;
-            d.n_zero = h->n_zero_rows;
+            d.csr5 = csr5_args(h, nullptr, nullptr);
             const int64_t g1 = ceil_div(h->ntiles, 8);
             for (int64_t g = 0; g < g1; ++g) t1.push_back(make_int4(b, T_CSR5, (int32_t)g, 0));
-            const int64_t n2 = h->ntiles > h->n_zero_rows ? h->ntiles : h->n_zero_rows;
-            for (int64_t g = 0; g < ceil_div(n2, 256); ++g) t2.push_back(make_int4(b, T_CSR5_CAL, (int32_t)g, 0));
+            if (h->ntiles == 0)
+                for (int64_t g = 0; g < ceil_div(h->n_zero_rows, 256); ++g)
+                    t1.push_back(make_int4(b, T_CSR5_ZERO, (int32_t)g, 0));
             break;
         }
         case SPMV_ELL:

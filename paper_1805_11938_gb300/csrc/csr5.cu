@@ -13,9 +13,9 @@
 //     seg_off[t] bit c = lane c holds no flagged slot;
 //   * a tile whose row span contains an empty row lists the row of every
 //     flagged slot (empty_rows[empty_ptr[t] ..]).
-// The product is two launches: one warp per tile, then a calibration pass
-// that adds the partial sums of rows crossing tile boundaries (carry) and
-// zeroes the empty rows.
+// The product is one launch, one warp per tile; rows crossing tile
+// boundaries are joined by the last of their tiles to finish (see csr5_tile),
+// and the tile warps share out the zeroing of the empty rows.
 #include "internal.cuh"
 #include "kernels.cuh"
 
@@ -151,7 +151,10 @@ int csr5_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     SPMV_TRY(h->alloc(&h->seg_off, (size_t)nt, "seg_off"));
     SPMV_TRY(h->alloc(&h->tile_idx, (size_t)(nt * S), "tile_idx"));
     SPMV_TRY(h->alloc(&h->tile_val, (size_t)(nt * S), "tile_val"));
-    SPMV_TRY(h->alloc(&h->carry, (size_t)nt, nullptr));
+    SPMV_TRY(h->alloc(&h->slot_head, (size_t)nt, nullptr));
+    SPMV_TRY(h->alloc(&h->slot_tail, (size_t)nt, nullptr));
+    SPMV_TRY(h->alloc(&h->join_cnt, (size_t)nt, nullptr));
+    if (nt > 0) SPMV_CUDA(cudaMemsetAsync(h->join_cnt, 0, sizeof(unsigned) * (size_t)nt, s));
     SPMV_TRY(h->alloc(&h->empty_ptr, (size_t)nt + 1, "empty_ptr"));
     Scratch tmp;
     int32_t *nflag = nullptr, *E = nullptr, *cnt = nullptr, *zoff = nullptr;
@@ -204,17 +207,20 @@ __global__ void __launch_bounds__(256) k_csr5(dev::Csr5Args a) {
     if (t < a.ntiles) dev::csr5_tile(a, t, threadIdx.x & 31);
 }
 
-__global__ void __launch_bounds__(256) k_csr5_cal(dev::Csr5Args a, const int32_t* __restrict__ zero_rows, int32_t nz) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    dev::csr5_calibrate(a, t, zero_rows, nz);
+__global__ void __launch_bounds__(256) k_csr5_zero(dev::Csr5Args a) {
+    dev::csr5_zero_all(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
+}
+
+dev::Csr5Args csr5_args(const spmv_handle* h, const double* x, double* y) {
+    return dev::Csr5Args{h->ptr, h->tile_ptr, h->flags, h->tile_idx, h->tile_val, h->empty_ptr, h->empty_rows,
+                         h->slot_head, h->slot_tail, h->join_cnt, h->zero_rows, h->n_zero_rows, h->nnz, h->ntiles,
+                         h->csr5_sigma, x, y};
 }
 
 int csr5_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s) {
-    dev::Csr5Args a{h->ptr, h->tile_ptr, h->flags, h->tile_idx, h->tile_val, h->empty_ptr, h->empty_rows, h->carry,
-                    h->nnz, h->ntiles, h->csr5_sigma, x, y};
+    const dev::Csr5Args a = csr5_args(h, x, y);
     if (h->ntiles > 0) k_csr5<<<grid_for(h->ntiles * 32, 256), 256, 0, s>>>(a);
-    const int64_t n2 = h->ntiles > h->n_zero_rows ? h->ntiles : h->n_zero_rows;
-    if (n2 > 0) k_csr5_cal<<<grid_for(n2, 256), 256, 0, s>>>(a, h->zero_rows, h->n_zero_rows);
+    else if (h->n_zero_rows > 0) k_csr5_zero<<<grid_for(h->n_zero_rows, 256), 256, 0, s>>>(a);
     SPMV_CUDA(cudaGetLastError());
     return SPMV_OK;
 }

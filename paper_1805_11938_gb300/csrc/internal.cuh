@@ -111,7 +111,9 @@ struct spmv_handle {
     int32_t* empty_rows = nullptr;
     int32_t* zero_rows = nullptr;  // the matrix's empty rows (y = 0)
     int32_t n_zero_rows = 0;
-    double* carry = nullptr;
+    double* slot_head = nullptr;  // per tile: its part of a row begun in an earlier tile
+    double* slot_tail = nullptr;  // per tile: its open last segment
+    unsigned* join_cnt = nullptr; // per start tile: tickets of the row's tiles (reset after use)
 
     // ELL and the ELL part of HYB
     spmv::EllPart ell;

@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 
 namespace spmv {
@@ -372,13 +373,18 @@ __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane
 //
 // A warp processes one tile of S = 32*sigma nonzeros: lane c walks its column
 // (nonzeros t*S + c*sigma + r, stored at t*S + r*32 + c, so each step is one
-// coalesced 256-byte load).  flags[t*32 + c] bit r marks a segment start.
-// Inside a lane, segments closed by a later flag in the same lane are
-// complete; the lane's last segment continues into the following lanes up to
-// the next lane holding a flag, which a segmented suffix sum over the lanes
-// (shuffles) supplies.  The tile's first segment, if it continues a row begun
-// in an earlier tile, goes to carry[t] instead of y; csr5_calibrate adds the
-// carries afterwards.
+// coalesced 256-byte load) with one DFMA per nonzero.  flags[t*32 + c] bit r
+// marks a segment start.  Inside a lane, segments closed by a later flag in the
+// same lane are complete; the lane's last segment continues into the following
+// lanes up to the next lane holding a flag, which a segmented suffix sum over
+// the lanes (shuffles) supplies.
+//
+// Rows that cross tile boundaries are finished in the same launch: the tile
+// where such a row starts stores its open last segment in slot_tail[t0], every
+// later tile the row reaches stores its head part in slot_head[t], and each
+// takes a ticket on cnt[t0]; the last of the row's tiles to finish adds the
+// slots in tile order and writes y (no waiting, deterministic order).  The
+// matrix's empty rows are zeroed by the tile warps, a share each.
 struct Csr5Args {
     const int32_t* ptr;
     const int32_t* tile_ptr;
@@ -387,13 +393,36 @@ struct Csr5Args {
     const double* tile_val;
     const int32_t* empty_ptr;
     const int32_t* empty_rows;
-    double* carry;
+    double* slot_head;
+    double* slot_tail;
+    unsigned* cnt;
+    const int32_t* zero_rows;
+    int32_t n_zero;
     int64_t nnz;
     int64_t ntiles;
     int32_t sigma;
     const double* x;
     double* y;
 };
+
+// Contribution of tile t to row r, which spans tiles t0 = ptr[r]/S .. t1;
+// the last contributor adds all of them in tile order.  Offsets are int32, so
+// the tile numbers come from 32-bit divisions.
+__device__ __forceinline__ void csr5_join(const Csr5Args& a, int32_t r, int64_t t, bool tail, double v, uint32_t S) {
+    const uint32_t t0 = (uint32_t)a.ptr[r] / S;
+    const uint32_t t1 = ((uint32_t)a.ptr[r + 1] - 1u) / S;
+    if (tail) a.slot_tail[t] = v;
+    else a.slot_head[t] = v;
+    // release our slot, acquire the others' (the last ticket sees every slot)
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> ticket(a.cnt[t0]);
+    const unsigned prev = ticket.fetch_add(1u, cuda::memory_order_acq_rel);
+    if (prev == t1 - t0) {
+        double acc = __ldcg(a.slot_tail + t0);
+        for (uint32_t u = t0 + 1; u <= t1; ++u) acc += __ldcg(a.slot_head + u);
+        ticket.store(0u, cuda::memory_order_relaxed);
+        a.y[r] = acc;
+    }
+}
 
 __device__ __forceinline__ void csr5_tile(const Csr5Args& a, int64_t t, int lane) {
     const int64_t S = 32LL * a.sigma;
@@ -407,6 +436,7 @@ __device__ __forceinline__ void csr5_tile(const Csr5Args& a, int64_t t, int lane
         const int v = __shfl_up_sync(kFull, yo, d);
         if (lane >= d) yo += v;
     }
+    const int total = __shfl_sync(kFull, yo, 31);  // flagged slots in the tile
     yo -= nf;
     const int32_t row0 = a.tile_ptr[t];
     const int32_t e0 = a.empty_ptr[t], e1 = a.empty_ptr[t + 1];
@@ -414,6 +444,8 @@ __device__ __forceinline__ void csr5_tile(const Csr5Args& a, int64_t t, int lane
     const bool cont = a.ptr[row0] != base;  // the tile starts inside row0
     const int64_t kl = base + (int64_t)lane * a.sigma;
     double cur = 0.0, head = 0.0;
+    double first = 0.0;  // lane 0: segment 0 when it closes inside the lane
+    bool first_join = false;
     int j = 0;  // segments of this lane seen so far
 #pragma unroll 8
     for (int r = 0; r < a.sigma; ++r) {
@@ -424,11 +456,15 @@ __device__ __forceinline__ void csr5_tile(const Csr5Args& a, int64_t t, int lane
         if ((f >> r) & 1u) {
             if (j == 0) {
                 head = cur;
-            } else {  // segment yo + j - 1 ends here, complete
+            } else {  // segment yo + j - 1 ends here, complete within the tile
                 const int g = yo + j - 1;
                 const int32_t row = listed ? a.empty_rows[e0 + g] : row0 + g;
-                if (g == 0 && cont) a.carry[t] = cur;
-                else a.y[row] = cur;
+                if (g == 0 && cont) {  // joined after the loop, keeping the loop lean
+                    first = cur;
+                    first_join = true;
+                } else {
+                    a.y[row] = cur;
+                }
             }
             ++j;
             cur = 0.0;
@@ -450,30 +486,26 @@ __device__ __forceinline__ void csr5_tile(const Csr5Args& a, int64_t t, int lane
     }
     double next = __shfl_down_sync(kFull, T, 1);
     if (lane == 31) next = 0.0;
+    if (first_join) csr5_join(a, row0, t, false, first, (uint32_t)S);
     if (nf > 0) {
         const int g = yo + nf - 1;
         const int32_t row = listed ? a.empty_rows[e0 + g] : row0 + g;
         const double tot = cur + next;
-        if (g == 0 && cont) a.carry[t] = tot;
-        else a.y[row] = tot;
+        if (g == 0 && cont) {
+            csr5_join(a, row, t, false, tot, (uint32_t)S);  // continues a row begun in an earlier tile
+        } else if (g == total - 1 && a.ptr[row + 1] > base + S) {
+            csr5_join(a, row, t, true, tot, (uint32_t)S);   // begins here, continues into later tiles
+        } else {
+            a.y[row] = tot;
+        }
     }
+    // the matrix's empty rows (y = 0), strided over the tile warps
+    for (int64_t z = t * 32 + lane; z < a.n_zero; z += a.ntiles * 32) a.y[a.zero_rows[z]] = 0.0;
 }
 
-// Adds the carries of tiles that begin inside a row: thread t handles the
-// first such tile of a row and the run of tiles after it continuing the same
-// row, in tile order.  Threads past the tiles write y = 0 for empty rows.
-__device__ __forceinline__ void csr5_calibrate(const Csr5Args& a, int64_t t, const int32_t* zero_rows,
-                                               int32_t n_zero) {
-    if (t < n_zero) a.y[zero_rows[t]] = 0.0;
-    if (t >= a.ntiles) return;
-    const int64_t S = 32LL * a.sigma;
-    const int32_t r = a.tile_ptr[t];
-    const int64_t start = a.ptr[r];
-    if (start == t * S) return;                       // tile t begins row r: no carry
-    if (t > 0 && a.tile_ptr[t - 1] == r && start < (t - 1) * S) return;  // not the first continuing tile
-    double acc = a.carry[t];
-    for (int64_t u = t + 1; u < a.ntiles && a.tile_ptr[u] == r; ++u) acc += a.carry[u];
-    a.y[r] += acc;
+// Zeroes the empty rows of a matrix without nonzeros (no tiles).
+__device__ __forceinline__ void csr5_zero_all(const Csr5Args& a, int64_t i) {
+    if (i < a.n_zero) a.y[a.zero_rows[i]] = 0.0;
 }
 
 }  // namespace dev
