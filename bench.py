@@ -56,6 +56,22 @@ def make_matrix(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def reduce_over_ranks(total_ms: float, flops: float, dist=None, device: str = "cpu") -> tuple:
+    """Whole-job rate over the ranks: the slowest rank's timed total (max) and
+    every rank's flops (sum); returns (max total ms, GFLOP/s).  Each rank
+    multiplies its own matrices (replicas or its share of a batch), so this is
+    the only exchange between ranks."""
+    if dist is not None:
+        import torch
+
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        f = torch.tensor([float(flops)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+        total_ms, flops = float(t.item()), float(f.item())
+    return total_ms, flops / (total_ms * 1e6)
+
+
 def algorithmic_bytes(fmt: int, info: dict) -> int:
     """Bytes a format must move per product: every stored nonzero once (8 B value + 4 B index),
     x and y once, plus the format's per-row / per-unit metadata (never the padding)."""
@@ -241,7 +257,8 @@ def run_batch(args, rank: int, world: int) -> None:
 
         dist.init_process_group("nccl")
     sp.lib()
-    model = sp.Model.load(sp.MODEL_PATH)
+    model_path = sp.MODEL_BATCH_PATH if os.path.exists(sp.MODEL_BATCH_PATH) else sp.MODEL_PATH
+    model = sp.Model.load(model_path)
     timer = autotune.Timer()
     n_mat = args.batch_count
     handles, xs, ys, infos, mats = [], [], [], [], []
@@ -298,12 +315,7 @@ def run_batch(args, rank: int, world: int) -> None:
     same = all(torch.equal(u, v) for u, v in zip(ys, ys2))
     tb = statistics.mean(t_b)
     ts = statistics.mean(t_s)
-    total_b = sum(t_b)
-    if dist:
-        t = torch.tensor([total_b], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_b = float(t.item())
-    value = world * 2.0 * total_nnz * args.steps / (total_b * 1e6)
+    total_b, value = reduce_over_ranks(sum(t_b), 2.0 * total_nnz * args.steps, dist, "cuda")
     ab = sum(algorithmic_bytes(i["fmt"], i) for i in infos)
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -316,7 +328,7 @@ def run_batch(args, rank: int, world: int) -> None:
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "matrices": n_mat,
                        "rows": total_rows, "nnz": total_nnz, "formats": dict(zip(FORMATS, counts)),
-                       "format_choice": "selector" if args.batch_format < 0 else "fixed",
+                       "format_choice": (os.path.basename(model_path) if args.batch_format < 0 else "fixed"),
                        "l2": "flushed: 256 MiB written before every timed step", "setup_s": t_setup,
                        "step": "one graph replay of the persistent batched kernel over all matrices"},
             "roofline": {"bound": "hbm", "achieved": ab / tb / 1e6, "peak": peak, "unit": "GB/s",
@@ -480,12 +492,7 @@ def main():
         t_wall = time.perf_counter() - t_wall
     step_ms = [s.elapsed_time(e) for s, _, e in ev]
     kern_ms = [m.elapsed_time(e) for _, m, e in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * 2.0 * a.nnz * args.steps / (total_ms * 1e6)
+    total_ms, value = reduce_over_ranks(sum(step_ms), 2.0 * a.nnz * args.steps, dist, "cuda")
     clocks = clk.summary()
 
     # ---- end to end: pinned host x in, y out, every step

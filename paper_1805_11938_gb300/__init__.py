@@ -325,4 +325,7 @@ def spmv_debug_fail_alloc(k: int) -> None:
     lib().spmv_debug_fail_alloc(int(k))
 
 
+# the selector trained on single-product times (spmv_select's default use), and
+# the one trained on throughput times, which picks formats inside a batch
 MODEL_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "selector_mlp.json")
+MODEL_BATCH_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "selector_mlp_batch.json")

@@ -1,14 +1,17 @@
 // Batched SpMV: many independent products y_b = A_b x_b, each matrix in its
-// own format, in one persistent launch (plus a second one for the passes that
-// must follow the first: the HYB COO tail).
+// own format, in one CUDA graph of at most three persistent launches:
+//     memset(counters) -> plain tasks -> CSR tiles -> HYB tails
+// The CSR tile tasks (CSR matrices and HYB COO tails) stage their nonzeros in
+// shared memory; every other task kind runs in a launch that reserves none,
+// which leaves the SM's unified L1/shared storage to L1, where the small x
+// vectors of the batch stay cached.  The HYB tails add into y after the ELL
+// part of their matrix is written, so they come last.
 //
-// The work list is built once on the host from the handles' unit counts:
-// task = {matrix, kind, index}.  A grid of (SMs x resident blocks) 256-thread
-// blocks takes tasks from an atomic counter until the list is exhausted (no
-// block ever waits on another).  build captures
-//     memset(counters) -> phase 1 -> phase 2
-// into a CUDA graph; run uploads the x/y pointer tables when they change and
-// replays the graph.
+// The work lists are built once on the host from the handles' unit counts:
+// task = {matrix, kind, index}.  Each launch is a grid of (SMs x resident
+// blocks) 256-thread blocks that take tasks from an atomic counter until the
+// list is exhausted (no block ever waits on another).  run uploads the x/y
+// pointer tables when they change and replays the graph.
 #include <cstring>
 #include <vector>
 
@@ -18,18 +21,18 @@
 namespace spmv {
 
 enum TaskKind : int32_t {
-    T_CSR = 0,       // 8 CSR warp units
+    T_CSR = 0,       // 8 CSR tiles (warp each)
     T_CSR5 = 1,      // 8 CSR5 tiles (warp each)
     T_ELL = 2,       // 512 ELL rows
     T_ELL_LONG = 3,  // one long ELL row
     T_SELL = 4,      // 8 SELL units (warp each)
     T_CSR5_ZERO = 5, // 256 empty rows of a CSR5 matrix without nonzeros
-    T_HYB_TAIL = 6   // 8 HYB tail warp units, adding into y
+    T_HYB_TAIL = 6,  // 8 HYB tail tiles, adding into y
+    T_CSR_ZERO = 7   // 256 rows of a CSR matrix without nonzeros
 };
 
 struct MatDesc {
     int32_t fmt, sell_r;
-    int32_t csr_units;
     int32_t ell_nb;
     const int32_t* long_rows;
     dev::CsrArgs csr;   // CSR, or the HYB tail (ADD)
@@ -47,8 +50,10 @@ struct BatchDev {
     double* const* ys;
 };
 
-__global__ void __launch_bounds__(256) k_batch(BatchDev B) {
-    __shared__ dev::CsrWarpSmem S[8];
+template <bool CSR>
+__global__ void __launch_bounds__(256, 4) k_batch(BatchDev B) {
+    extern __shared__ __align__(16) unsigned char batch_smem[];
+    dev::CsrWarpSmem* S = reinterpret_cast<dev::CsrWarpSmem*>(batch_smem);  // CSR: one slice per warp
     __shared__ double red[8];
     __shared__ int task_sh;
     for (;;) {
@@ -62,21 +67,23 @@ __global__ void __launch_bounds__(256) k_batch(BatchDev B) {
         const double* x = B.xs[t.x];
         double* y = B.ys[t.x];
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        switch (t.y) {
-            case T_CSR: {
-                dev::CsrArgs a = md.csr;
-                a.x = x;
-                a.y = y;
-                const int32_t u = t.z * 8 + warp;
-                if (u < md.csr_units) dev::csr_warp_unit<false>(a, u, S[warp], lane);
-                break;
+        if (CSR) {
+            dev::CsrArgs a = md.csr;
+            a.x = x;
+            a.y = y;
+            const int32_t u = t.z * 8 + warp;
+            if (u < a.ntiles) {
+                if (t.y == T_HYB_TAIL) dev::csr_tile<true>(a, u, S[warp], lane);
+                else dev::csr_tile<false>(a, u, S[warp], lane);
             }
-            case T_HYB_TAIL: {
+            continue;
+        }
+        switch (t.y) {
+            case T_CSR_ZERO: {
                 dev::CsrArgs a = md.csr;
                 a.x = x;
                 a.y = y;
-                const int32_t u = t.z * 8 + warp;
-                if (u < md.csr_units) dev::csr_warp_unit<true>(a, u, S[warp], lane);
+                dev::csr_zero(a, (int64_t)t.z * 256 + threadIdx.x);
                 break;
             }
             case T_CSR5: {
@@ -131,16 +138,14 @@ struct spmv_batch {
     int32_t count = 0;
     std::vector<spmv_handle*> handles;
     spmv::MatDesc* d_mats = nullptr;
-    int4* d_tasks1 = nullptr;
-    int4* d_tasks2 = nullptr;
-    int32_t n1 = 0, n2 = 0;
-    unsigned* d_counters = nullptr;  // 2
+    int4* d_tasks[3] = {nullptr, nullptr, nullptr};  // plain, CSR tiles, HYB tails
+    int32_t n_tasks[3] = {0, 0, 0};
+    unsigned* d_counters = nullptr;  // 3
     const double** d_xs = nullptr;
     double** d_ys = nullptr;
     std::vector<const double*> xs;
     std::vector<double*> ys;
-    size_t smem = 0;
-    int grid = 0;
+    int grid_plain = 0, grid_csr = 0;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphExec_t exec_sep = nullptr;
@@ -151,8 +156,7 @@ struct spmv_batch {
         if (exec_sep) cudaGraphExecDestroy(exec_sep);
         if (cap) cudaStreamDestroy(cap);
         spmv::dev_free(d_mats);
-        spmv::dev_free(d_tasks1);
-        spmv::dev_free(d_tasks2);
+        for (int i = 0; i < 3; ++i) spmv::dev_free(d_tasks[i]);
         spmv::dev_free(d_counters);
         spmv::dev_free(d_xs);
         spmv::dev_free(d_ys);
@@ -163,15 +167,18 @@ namespace spmv {
 
 dev::Csr5Args csr5_args(const spmv_handle* h, const double* x, double* y);
 
-static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, std::vector<int4>& t2, int32_t b) {
+// Appends matrix b's tasks to the plain list t1, the CSR tile list tc and the
+// HYB tail list t2.
+static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, std::vector<int4>& tc,
+                      std::vector<int4>& t2, int32_t b) {
     memset(&d, 0, sizeof d);
     d.fmt = h->fmt;
     switch (h->fmt) {
         case SPMV_CSR:
-            d.csr = dev::CsrArgs{h->cu.units, h->ptr, h->idx, h->val, nullptr, nullptr, nullptr, h->cu.partial,
-                                 h->cu.counters};
-            d.csr_units = h->cu.n;
-            for (int64_t g = 0; g < ceil_div(h->cu.n, 8); ++g) t1.push_back(make_int4(b, T_CSR, (int32_t)g, 0));
+            d.csr = csr_tile_args(h->cu, h->ptr, h->idx, h->val, nullptr, nullptr, nullptr);
+            for (int64_t g = 0; g < ceil_div(h->cu.n, 8); ++g) tc.push_back(make_int4(b, T_CSR, (int32_t)g, 0));
+            if (h->cu.n == 0)
+                for (int64_t g = 0; g < ceil_div(h->m, 256); ++g) t1.push_back(make_int4(b, T_CSR_ZERO, (int32_t)g, 0));
             break;
         case SPMV_CSR5: {
             d.csr5 = csr5_args(h, nullptr, nullptr);
@@ -192,9 +199,8 @@ static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, s
             if (h->fmt == SPMV_ELL)
                 for (int32_t j = 0; j < h->ell.n_long; ++j) t1.push_back(make_int4(b, T_ELL_LONG, j, 0));
             if (h->fmt == SPMV_HYB && h->n_tail_rows > 0) {
-                d.csr = dev::CsrArgs{h->tail_units.units, h->tail_ptr, h->tail_col, h->tail_val, h->tail_rows, nullptr,
-                                     nullptr, h->tail_units.partial, h->tail_units.counters};
-                d.csr_units = h->tail_units.n;
+                d.csr = csr_tile_args(h->tail_units, h->tail_ptr, h->tail_col, h->tail_val, h->tail_rows, nullptr,
+                                      nullptr);
                 for (int64_t g = 0; g < ceil_div(h->tail_units.n, 8); ++g)
                     t2.push_back(make_int4(b, T_HYB_TAIL, (int32_t)g, 0));
             }
@@ -213,11 +219,13 @@ static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>& t1, s
 static int capture_batch(spmv_batch* bt) {
     cudaGraph_t g = nullptr;
     SPMV_CUDA(cudaStreamBeginCapture(bt->cap, cudaStreamCaptureModeThreadLocal));
-    cudaMemsetAsync(bt->d_counters, 0, 2 * sizeof(unsigned), bt->cap);
-    BatchDev a1{bt->d_mats, bt->d_tasks1, bt->n1, bt->d_counters, bt->d_xs, bt->d_ys};
-    if (bt->n1 > 0) k_batch<<<bt->grid, 256, bt->smem, bt->cap>>>(a1);
-    BatchDev a2{bt->d_mats, bt->d_tasks2, bt->n2, bt->d_counters + 1, bt->d_xs, bt->d_ys};
-    if (bt->n2 > 0) k_batch<<<bt->grid, 256, bt->smem, bt->cap>>>(a2);
+    cudaMemsetAsync(bt->d_counters, 0, 3 * sizeof(unsigned), bt->cap);
+    for (int i = 0; i < 3; ++i) {
+        if (bt->n_tasks[i] == 0) continue;
+        BatchDev a{bt->d_mats, bt->d_tasks[i], bt->n_tasks[i], bt->d_counters + i, bt->d_xs, bt->d_ys};
+        if (i == 0) k_batch<false><<<bt->grid_plain, 256, 0, bt->cap>>>(a);
+        else k_batch<true><<<bt->grid_csr, 256, dev::kCsrSmemBytes, bt->cap>>>(a);
+    }
     cudaError_t e = cudaStreamEndCapture(bt->cap, &g);
     if (e != cudaSuccess) return cuda_error(e, "batch graph capture");
     e = cudaGraphInstantiate(&bt->exec, g, 0);
@@ -263,15 +271,14 @@ int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t st
     bt->count = count;
     bt->handles.assign(handles, handles + count);
     std::vector<MatDesc> mats(count);
-    std::vector<int4> t1, t2;
-    for (int32_t b = 0; b < count; ++b) fill_desc(handles[b], mats[b], t1, t2, b);
-    bt->n1 = (int32_t)t1.size();
-    bt->n2 = (int32_t)t2.size();
-    bt->smem = 0;
+    std::vector<int4> lists[3];  // plain, CSR tiles, HYB tails
+    for (int32_t b = 0; b < count; ++b) fill_desc(handles[b], mats[b], lists[0], lists[1], lists[2], b);
     int st = dev_malloc((void**)&bt->d_mats, sizeof(MatDesc) * count);
-    if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_tasks1, sizeof(int4) * (t1.size() + 1));
-    if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_tasks2, sizeof(int4) * (t2.size() + 1));
-    if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_counters, 2 * sizeof(unsigned));
+    for (int i = 0; i < 3; ++i) {
+        bt->n_tasks[i] = (int32_t)lists[i].size();
+        if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_tasks[i], sizeof(int4) * (lists[i].size() + 1));
+    }
+    if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_counters, 3 * sizeof(unsigned));
     if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_xs, sizeof(double*) * count);
     if (st == SPMV_OK) st = dev_malloc((void**)&bt->d_ys, sizeof(double*) * count);
     if (st != SPMV_OK) {
@@ -279,22 +286,26 @@ int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t st
         return st;
     }
     cudaError_t e = cudaMemcpy(bt->d_mats, mats.data(), sizeof(MatDesc) * count, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !t1.empty())
-        e = cudaMemcpy(bt->d_tasks1, t1.data(), sizeof(int4) * t1.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !t2.empty())
-        e = cudaMemcpy(bt->d_tasks2, t2.data(), sizeof(int4) * t2.size(), cudaMemcpyHostToDevice);
+    for (int i = 0; i < 3; ++i)
+        if (e == cudaSuccess && !lists[i].empty())
+            e = cudaMemcpy(bt->d_tasks[i], lists[i].data(), sizeof(int4) * lists[i].size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(bt->d_xs, 0, sizeof(double*) * count);
     if (e == cudaSuccess) e = cudaMemset(bt->d_ys, 0, sizeof(double*) * count);
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0, per_sm_plain = 0, per_sm_csr = 0;
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dev::kCsrSmemBytes);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, 256, bt->smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_plain, k_batch<false>, 256, 0);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_csr, k_batch<true>, 256, dev::kCsrSmemBytes);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         delete bt;
         return cuda_error(e, "spmv_batch_build");
     }
-    bt->grid = sms * (per_sm > 0 ? per_sm : 1);
+    bt->grid_plain = sms * (per_sm_plain > 0 ? per_sm_plain : 1);
+    bt->grid_csr = sms * (per_sm_csr > 0 ? per_sm_csr : 1);
     bt->xs.assign(count, nullptr);
     bt->ys.assign(count, nullptr);
     st = capture_batch(bt);

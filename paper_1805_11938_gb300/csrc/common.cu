@@ -266,67 +266,42 @@ int64_t resolve_cap(const spmv_params& p) {
     return (int64_t)(0.9 * (double)fr);
 }
 
-// ------------------------------------------------------------- CSR units
+// ------------------------------------------------------------- CSR tiles
 //
-// Row i opens a unit when i = 0, when row i or row i-1 holds more than
-// H = kCsrW/2 nonzeros, when i crosses a multiple of kCsrRows rows, or when
-// ptr[i] enters a new H-aligned window of nonzeros.  A unit of short rows
-// therefore holds at most kCsrRows rows and fewer than 2H = kCsrW nonzeros.
-// A row longer than kCsrChunk becomes ceil(len / kCsrChunk) chunk units.
+// Tile u covers nonzeros [u*W, (u+1)*W); tile_row[u] is the first row whose
+// pointer is at or after u*W (a lower bound over ptr[0..rows]), so the rows
+// starting in tile u are tile_row[u] .. tile_row[u+1]-1.  tile_row[ntiles] =
+// rows, so the last tile also takes the trailing empty rows.
 
-__global__ void k_unit_counts(const int32_t* __restrict__ ptr, int32_t m, int32_t* __restrict__ cnt) {
-    constexpr int32_t H = dev::kCsrW / 2, CH = dev::kCsrChunk;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i > m) return;
-    if (i == m) {
-        cnt[m] = 0;
+__global__ void k_tile_row(const int32_t* __restrict__ ptr, int32_t rows, int32_t nt, int32_t* __restrict__ tile_row) {
+    const int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (u > nt) return;
+    if (u == nt) {
+        tile_row[nt] = rows;
         return;
     }
-    const int32_t p = ptr[i], len = ptr[i + 1] - p;
-    bool start = (i == 0) || len > H;
-    if (i > 0) {
-        const int32_t pp = ptr[i - 1];
-        start = start || (p - pp > H) || (i / dev::kCsrRows != (i - 1) / dev::kCsrRows) || (p / H != pp / H);
+    const int64_t k = u * dev::kCsrW;
+    int32_t lo = 0, hi = rows;  // ptr[rows] = nnz > k
+    while (lo < hi) {
+        const int32_t mid = lo + (hi - lo) / 2;
+        if (ptr[mid] >= k) hi = mid;
+        else lo = mid + 1;
     }
-    cnt[i] = start ? (len > CH ? (len + CH - 1) / CH : 1) : 0;
+    tile_row[u] = lo;
 }
 
-__global__ void k_unit_fill(const int32_t* __restrict__ ptr, int32_t m, const int32_t* __restrict__ cnt,
-                            const int32_t* __restrict__ off, int4* __restrict__ units) {
-    constexpr int32_t CH = dev::kCsrChunk;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i > m) return;
-    if (i == m) {
-        units[off[m]] = make_int4(m, ptr[m], -1, 0);
-        return;
-    }
-    const int32_t c = cnt[i];
-    if (c == 0) return;
-    const int32_t p = ptr[i], len = ptr[i + 1] - p;
-    const bool split = len > CH;
-    for (int32_t k = 0; k < c; ++k)
-        units[off[i] + k] = make_int4((int32_t)i, p + k * CH, split ? k : -1, split ? c : 0);
-}
-
-int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t rows, const char* prefix,
+int build_csr_tiles(spmv_handle* h, CsrTiles& ct, const int32_t* ptr, int32_t rows, int64_t nnz, const char* prefix,
                     cudaStream_t s) {
-    Scratch tmp;
-    int32_t *cnt = nullptr, *off = nullptr;
-    SPMV_TRY(tmp.get(&cnt, (size_t)rows + 1));
-    SPMV_TRY(tmp.get(&off, (size_t)rows + 2));
-    k_unit_counts<<<grid_for((int64_t)rows + 1, 256), 256, 0, s>>>(ptr, rows, cnt);
-    SPMV_CUDA(cudaGetLastError());
-    SPMV_TRY(exclusive_scan<int32_t>(cnt, off, (int64_t)rows + 1, s, tmp));
-    int32_t n_units = 0;
-    SPMV_CUDA(cudaMemcpyAsync(&n_units, off + rows, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    SPMV_CUDA(cudaStreamSynchronize(s));
-    cu.n = n_units;
+    ct.rows = rows;
+    ct.nnz = nnz;
+    ct.n = (int32_t)ceil_div(nnz, dev::kCsrW);
     std::string pre = prefix ? prefix : "";
-    SPMV_TRY(h->alloc(&cu.units, (size_t)n_units + 1, (pre + "units").c_str()));
-    SPMV_TRY(h->alloc(&cu.partial, (size_t)n_units + 1, nullptr));
-    SPMV_TRY(h->alloc(&cu.counters, (size_t)n_units + 1, nullptr));
-    SPMV_CUDA(cudaMemsetAsync(cu.counters, 0, sizeof(unsigned) * ((size_t)n_units + 1), s));
-    k_unit_fill<<<grid_for((int64_t)rows + 1, 256), 256, 0, s>>>(ptr, rows, cnt, off, cu.units);
+    SPMV_TRY(h->alloc(&ct.tile_row, (size_t)ct.n + 1, (pre + "tile_row").c_str()));
+    SPMV_TRY(h->alloc(&ct.slot_head, (size_t)ct.n + 1, nullptr));
+    SPMV_TRY(h->alloc(&ct.slot_tail, (size_t)ct.n + 1, nullptr));
+    SPMV_TRY(h->alloc(&ct.cnt, (size_t)ct.n + 1, nullptr));
+    SPMV_CUDA(cudaMemsetAsync(ct.cnt, 0, sizeof(unsigned) * ((size_t)ct.n + 1), s));
+    k_tile_row<<<grid_for((int64_t)ct.n + 1, 256), 256, 0, s>>>(ptr, rows, ct.n, ct.tile_row);
     SPMV_CUDA(cudaGetLastError());
     SPMV_CUDA(cudaStreamSynchronize(s));
     return SPMV_OK;

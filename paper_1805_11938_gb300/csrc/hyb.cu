@@ -4,7 +4,7 @@
 //
 // The tail is kept grouped by row (tail_rows, tail_ptr: COO sorted by row,
 // CSR order inside a row), so it is summed without atomics: the ELL kernel
-// writes every y_i, then the CSR row-block kernel adds each tail row's sum to
+// writes every y_i, then the CSR tile kernel adds each tail row's sum to
 // its own y_i (one writer per row, stream-ordered after the ELL part).
 #include "internal.cuh"
 #include "kernels.cuh"
@@ -131,7 +131,8 @@ int hyb_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
                                          h->tail_val);
         SPMV_CUDA(cudaGetLastError());
     }
-    SPMV_TRY(build_csr_units(h, h->tail_units, h->tail_ptr, ntr, "tail_", s));
+    SPMV_TRY(build_csr_tiles(h, h->tail_units, h->tail_ptr, ntr, nt, "tail_", s));
+    SPMV_TRY(csr_prepare(h->tail_units));
     h->stored_slots += nt;
     h->aux[0] = nt;
     h->aux[1] = ntr;
@@ -143,7 +144,7 @@ int hyb_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
 int hyb_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s) {
     SPMV_TRY(ell_launch(h->ell, h->m, 0x7fffffff, x, y, s));
     if (h->n_tail_rows > 0)
-        SPMV_TRY(csr_units_launch(h->tail_units, h->tail_ptr, h->tail_col, h->tail_val, h->tail_rows, x, y, true, s));
+        SPMV_TRY(csr_tiles_launch(h->tail_units, h->tail_ptr, h->tail_col, h->tail_val, h->tail_rows, x, y, true, s));
     return SPMV_OK;
 }
 

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/spmv.h"
+#include "kernels.cuh"
 
 namespace spmv {
 
@@ -59,14 +60,17 @@ struct NamedArray {
     int32_t elem_bytes;
 };
 
-// CSR warp units (also used for the HYB COO tail): units[u] = {r0, k0, c, nch},
-// the unit covers rows [r0, units[u+1].x) and nonzeros [k0, units[u+1].y);
-// c >= 0 marks chunk c of nch of one long row.
-struct CsrUnits {
-    int4* units = nullptr;      // n + 1 entries (sentinel {rows, nnz, -1, 0})
+// CSR nonzero tiles (also used for the HYB COO tail): n tiles of kCsrW
+// nonzeros, tile_row[u] = first row starting at or after u*kCsrW.
+struct CsrTiles {
+    int32_t* tile_row = nullptr;  // n + 1 entries
     int32_t n = 0;
-    double* partial = nullptr;  // per unit, for split long rows
-    unsigned* counters = nullptr;
+    int32_t rows = 0;
+    int64_t nnz = 0;
+    int32_t grid = 0;             // persistent grid of the tile kernel
+    double* slot_head = nullptr;  // per tile, for rows crossing tiles
+    double* slot_tail = nullptr;
+    unsigned* cnt = nullptr;
 };
 
 struct EllPart {  // column-major ELL: slot s of row i at s*ld + i
@@ -96,7 +100,7 @@ struct spmv_handle {
     int32_t* ptr = nullptr;
     int32_t* idx = nullptr;
     double* val = nullptr;
-    spmv::CsrUnits cu;
+    spmv::CsrTiles cu;
 
     // CSR5
     int32_t csr5_sigma = 0;
@@ -138,7 +142,7 @@ struct spmv_handle {
     int32_t* tail_ptr = nullptr;
     int32_t* tail_col = nullptr;
     double* tail_val = nullptr;
-    spmv::CsrUnits tail_units;
+    spmv::CsrTiles tail_units;
 
     template <class T>
     int alloc(T** p, size_t count, const char* name) {
@@ -166,15 +170,19 @@ int row_lengths(const int32_t* ptr, int32_t m, int32_t* len, cudaStream_t s);
 int max_i32(const int32_t* a, int64_t n, int32_t* result_host, cudaStream_t s, Scratch& tmp);
 int copy_csr(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
 int64_t resolve_cap(const spmv_params& p);
-// Warp units of CSR row blocks over (ptr, rows).
-int build_csr_units(spmv_handle* h, CsrUnits& cu, const int32_t* ptr, int32_t rows, const char* prefix,
+// Nonzero tiles over the CSR arrays (ptr, rows, nnz).
+int build_csr_tiles(spmv_handle* h, CsrTiles& ct, const int32_t* ptr, int32_t rows, int64_t nnz, const char* prefix,
                     cudaStream_t s);
 
 // ---- per-format conversion and launch
 int csr_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
 int csr_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s);
-int csr_units_launch(const CsrUnits& cu, const int32_t* ptr, const int32_t* idx, const double* val,
+dev::CsrArgs csr_tile_args(const CsrTiles& ct, const int32_t* ptr, const int32_t* idx, const double* val,
+                           const int32_t* row_map, const double* x, double* y);
+int csr_tiles_launch(const CsrTiles& ct, const int32_t* ptr, const int32_t* idx, const double* val,
                      const int32_t* row_map, const double* x, double* y, bool add, cudaStream_t s);
+// Opens the tile kernels' dynamic shared memory and sizes their persistent grid.
+int csr_prepare(CsrTiles& ct);
 
 int csr5_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s);
 int csr5_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s);

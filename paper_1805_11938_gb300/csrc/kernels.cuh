@@ -58,44 +58,52 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
 // Random gathers of x cost one L1 wavefront per lane, so every other load is
 // coalesced.
 //
-// Work is split into warp units (units[u] = {r0, k0, c, nch}; the next unit
-// gives r1 and k1):
-//  * c = -1, several rows (fewer than kCsrW nonzeros, at most kCsrRows rows):
-//    the warp stages values and column indices in its shared slice with
-//    coalesced loads, then lane l walks the contiguous chunk
-//    [l*CT, l*CT + CT) (CT odd: conflict-free shared accesses), gathering x
-//    and issuing one DFMA per nonzero, writing every row that begins and ends
-//    in its chunk;
-//    a row begun in an earlier lane leaves its partial in shared memory and
-//    the lane owning the row's start adds those partials in lane order;
-//  * c = -1, one row longer than the unit budget: lanes stride the row with
-//    four accumulators, then one warp reduction;
-//  * c >= 0: chunk c of nch of a row longer than kCsrChunk; partials go to
-//    partial[u] and the last chunk to finish (atomic ticket) adds them in
-//    order.
-constexpr int kCsrW = 416;      // a multi-row unit holds fewer nonzeros than this
-constexpr int kCsrRows = 64;    // and at most this many rows
-constexpr int kCsrChunk = 1024; // rows longer than this are split into chunks
+// The CSR arrays are used as they are; the work is cut by nonzeros, not by
+// rows: tile u is nonzeros [u*W, (u+1)*W) (W = 32*kCsrCT), one warp each, so
+// every warp carries the same load whatever the row lengths.  A row gets
+// lanes in proportion to its length: a lane walks many short rows, a long row
+// spans many lanes or tiles.  The warp
+//  1. stages the tile's values and column indices in its shared slice with
+//     coalesced loads;
+//  2. reads the pointers of the rows that start in the tile (rows
+//     tile_row[u] .. tile_row[u+1]-1), writes y = 0 for the empty ones, and
+//     for each nonempty one sets a bit in a per-lane flag word (bit r of
+//     lane l: nonzero l*kCsrCT + r begins a row) and appends its row number
+//     to the tile's segment list (ballots keep the list in row order);
+//  3. lane l walks its kCsrCT nonzeros with one gather and one DFMA each,
+//     writing every row that begins and ends in its chunk; a segmented
+//     suffix sum over the lanes (shuffles) completes the rows spanning lanes;
+//  4. a row that crosses tile boundaries is finished by the last of its tiles
+//     to arrive: each stores its part in a per-tile slot and takes a ticket,
+//     and the last ticket holder adds the slots in tile order (no waiting,
+//     deterministic order).
+constexpr int kCsrCT = 13;          // nonzeros per lane (odd: conflict-free shared accesses)
+constexpr int kCsrW = 32 * kCsrCT;  // nonzeros per tile
 
 struct CsrArgs {
-    const int4* units;
+    const int32_t* tile_row;  // ntiles + 1: first row with ptr >= u*W; tile_row[ntiles] = rows
     const int32_t* ptr;
     const int32_t* idx;
     const double* val;
-    const int32_t* row_map;  // ADD mode: y[row_map[r]] += sum; else y[r] = sum
+    const int32_t* row_map;   // ADD mode: y[row_map[r]] += sum; else y[r] = sum
+    double* slot_head;        // per tile: its part of a row begun in an earlier tile
+    double* slot_tail;        // per tile: its open last segment
+    unsigned* cnt;            // per start tile: tickets of the row's tiles (reset after use)
+    int32_t rows;
+    int32_t nnz;
+    int32_t ntiles;
     const double* x;
     double* y;
-    double* partial;
-    unsigned* counters;
 };
 
 struct CsrWarpSmem {
     double sv[kCsrW];
-    double hv[32];
     int32_t si[kCsrW];
-    int32_t sp[kCsrRows + 1];
-    int32_t hr[32];
+    int32_t rid[kCsrW + 1];  // row of each segment of the tile, in order
+    uint32_t fl[32];
 };
+constexpr int kCsrWarps = 8;  // warps (tiles in flight) per 256-thread block
+constexpr size_t kCsrSmemBytes = sizeof(CsrWarpSmem) * kCsrWarps;
 
 template <bool ADD>
 __device__ __forceinline__ void csr_put(const CsrArgs& a, int32_t r, double s) {
@@ -107,116 +115,143 @@ __device__ __forceinline__ void csr_put(const CsrArgs& a, int32_t r, double s) {
     }
 }
 
-// Sum of val[k] * x[idx[k]] over [k0, k1) by one warp; valid in every lane.
-__device__ __forceinline__ double warp_range_sum(const int32_t* __restrict__ idx, const double* __restrict__ val,
-                                                 const double* __restrict__ x, int64_t k0, int64_t k1, int lane) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int64_t k = k0 + lane;
-    for (; k + 96 < k1; k += 128) {
-        const int32_t c0 = __ldcs(idx + k), c1 = __ldcs(idx + k + 32), c2 = __ldcs(idx + k + 64),
-                      c3 = __ldcs(idx + k + 96);
-        const double v0 = __ldcs(val + k), v1 = __ldcs(val + k + 32), v2 = __ldcs(val + k + 64),
-                     v3 = __ldcs(val + k + 96);
-        s0 = fma(v0, ldx(x, c0), s0);
-        s1 = fma(v1, ldx(x, c1), s1);
-        s2 = fma(v2, ldx(x, c2), s2);
-        s3 = fma(v3, ldx(x, c3), s3);
+// Tile t's part v of row r (tail: r begins in t; else r began earlier).
+template <bool ADD>
+__device__ __forceinline__ void csr_join(const CsrArgs& a, int32_t r, int32_t t, bool tail, double v) {
+    const uint32_t t0 = (uint32_t)a.ptr[r] / (uint32_t)kCsrW;
+    const uint32_t t1 = ((uint32_t)a.ptr[r + 1] - 1u) / (uint32_t)kCsrW;
+    if (tail) a.slot_tail[t] = v;
+    else a.slot_head[t] = v;
+    // release our slot, acquire the others' (the last ticket sees every slot)
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> ticket(a.cnt[t0]);
+    const unsigned prev = ticket.fetch_add(1u, cuda::memory_order_acq_rel);
+    if (prev == t1 - t0) {
+        double acc = __ldcg(a.slot_tail + t0);
+#pragma unroll 8
+        for (uint32_t u = t0 + 1; u <= t1; ++u) acc += __ldcg(a.slot_head + u);
+        ticket.store(0u, cuda::memory_order_relaxed);
+        csr_put<ADD>(a, r, acc);
     }
-    for (; k < k1; k += 32) s0 = fma(__ldcs(val + k), ldx(x, __ldcs(idx + k)), s0);
-    return warp_sum((s0 + s1) + (s2 + s3));
 }
 
 template <bool ADD>
-__device__ __forceinline__ void csr_warp_unit(const CsrArgs& a, int32_t u, CsrWarpSmem& S, int lane) {
-    const int4 U = a.units[u];
-    const int4 V = a.units[u + 1];
-    const int32_t r0 = U.x;
-    const int32_t k0 = U.y, k1 = V.y;
-    if (U.z >= 0) {  // chunk U.z of U.w of one long row
-        const double s = warp_range_sum(a.idx, a.val, a.x, k0, k1, lane);
-        if (lane == 0) {
-            const int32_t first = u - U.z;
-            a.partial[u] = s;
-            __threadfence();
-            const unsigned prev = atomicAdd(a.counters + first, 1u);
-            if (prev == (unsigned)(U.w - 1)) {
-                __threadfence();
-                double acc = 0.0;
-#pragma unroll 8
-                for (int32_t c = 0; c < U.w; ++c) acc += __ldcg(a.partial + first + c);
-                a.counters[first] = 0u;
-                csr_put<ADD>(a, r0, acc);
-            }
+__device__ __forceinline__ void csr_tile(const CsrArgs& a, int32_t t, CsrWarpSmem& S, int lane) {
+    const int64_t base = (int64_t)t * kCsrW;
+    const int32_t n = (int32_t)min((int64_t)kCsrW, (int64_t)a.nnz - base);  // >= 1
+    const int32_t r0 = a.tile_row[t], r1 = a.tile_row[t + 1];
+    // 1. stage values and column indices (coalesced)
+    const double* __restrict__ vb = a.val + base;
+    const int32_t* __restrict__ ib = a.idx + base;
+    if (n == kCsrW) {
+#pragma unroll
+        for (int q = 0; q < kCsrCT; ++q) {
+            S.sv[q * 32 + lane] = __ldcs(vb + q * 32 + lane);
+            S.si[q * 32 + lane] = __ldcs(ib + q * 32 + lane);
         }
-        return;
+    } else {
+        for (int j = lane; j < n; j += 32) {
+            S.sv[j] = __ldcs(vb + j);
+            S.si[j] = __ldcs(ib + j);
+        }
     }
-    const int32_t nrows = V.x - r0;
-    const int32_t n = k1 - k0;
-    if (nrows == 1 && n >= kCsrW) {  // one long row
-        const double s = warp_range_sum(a.idx, a.val, a.x, k0, k1, lane);
-        if (lane == 0) csr_put<ADD>(a, r0, s);
-        return;
-    }
-    for (int32_t t = lane; t <= nrows; t += 32) S.sp[t] = a.ptr[r0 + t] - k0;
-    const double* __restrict__ vb = a.val + k0;
-    const int32_t* __restrict__ ib = a.idx + k0;
-#pragma unroll 4
-    for (int32_t j = lane; j < n; j += 32) {
-        S.sv[j] = __ldcs(vb + j);
-        S.si[j] = __ldcs(ib + j);
+    S.fl[lane] = lane == 0 ? 1u : 0u;  // the tile's first nonzero always opens a segment
+    __syncwarp();
+    // 2. the rows starting in the tile
+    const bool cont = a.ptr[r0] > base;  // nonzero `base` lies in row r0 - 1, begun earlier
+    if (cont && lane == 0) S.rid[0] = r0 - 1;
+    int32_t nseg = cont ? 1 : 0;
+    for (int32_t rb = r0; rb < r1; rb += 32) {
+        const int32_t r = rb + lane;
+        int32_t p = 0;
+        bool nonempty = false;
+        if (r < r1) {
+            p = a.ptr[r];
+            nonempty = a.ptr[r + 1] > p;
+            if (!ADD && !nonempty) a.y[r] = 0.0;
+        }
+        const unsigned mask = __ballot_sync(kFull, nonempty);
+        if (nonempty) {
+            const int32_t pos = (int32_t)(p - base);
+            S.rid[nseg + __popc(mask & ((1u << lane) - 1u))] = r;
+            atomicOr(&S.fl[pos / kCsrCT], 1u << (pos % kCsrCT));
+        }
+        nseg += __popc(mask);
     }
     __syncwarp();
-    for (int32_t t = lane; t < nrows; t += 32)
-        if (S.sp[t + 1] == S.sp[t]) csr_put<ADD>(a, r0 + t, 0.0);  // empty rows
-    const int32_t CT = ((n + 31) >> 5) | 1;
-    const int32_t c0 = lane * CT;
-    const int32_t c1 = c0 + CT < n ? c0 + CT : n;
-    double s = 0.0, head = 0.0;
-    int32_t head_row = -1, owned_tail = -1;
-    if (c0 < c1) {
-        int32_t lo = 0, hi = nrows - 1;
-        while (lo < hi) {  // the row holding nonzero c0
-            const int32_t mid = (lo + hi + 1) >> 1;
-            if (S.sp[mid] <= c0) lo = mid;
-            else hi = mid - 1;
-        }
-        int32_t row = lo;
-        int32_t end = S.sp[row + 1];
-        bool own = S.sp[row] == c0;
-#pragma unroll 4
-        for (int32_t k = c0; k < c1; ++k) {
-            const double xv = ldx(a.x, S.si[k]);
-            if (k == end) {
-                if (own) csr_put<ADD>(a, r0 + row, s);
-                else { head = s; head_row = row; }
-                s = 0.0;
-                own = true;
-                do {
-                    ++row;
-                    end = S.sp[row + 1];
-                } while (end == k);
+    // 3. the walk
+    const uint32_t f = S.fl[lane];
+    const int nf = __popc(f);
+    int yo = nf;  // inclusive count of flags up to this lane
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(kFull, yo, d);
+        if (lane >= d) yo += v;
+    }
+    const int total = __shfl_sync(kFull, yo, 31);  // segments in the tile
+    yo -= nf;
+    const int c0 = lane * kCsrCT;
+    double cur = 0.0, head = 0.0;
+    double first = 0.0;  // lane 0: segment 0 when it continues a row and closes inside the lane
+    bool first_join = false;
+    int j = 0;  // segments of this lane seen so far
+#pragma unroll
+    for (int r = 0; r < kCsrCT; ++r) {
+        const int k = c0 + r;
+        const bool valid = k < n;  // false only in the last, partial tile
+        const double v = valid ? S.sv[k] : 0.0;
+        const double xv = valid ? ldx(a.x, S.si[k]) : 0.0;
+        if ((f >> r) & 1u) {
+            if (j == 0) {
+                head = cur;
+            } else {  // segment yo + j - 1 ends here, complete within the tile
+                const int g = yo + j - 1;
+                if (g == 0 && cont) {  // joined after the walk, keeping the loop lean
+                    first = cur;
+                    first_join = true;
+                } else {
+                    csr_put<ADD>(a, S.rid[g], cur);
+                }
             }
-            s = fma(S.sv[k], xv, s);
+            ++j;
+            cur = 0.0;
         }
-        if (end == c1) {  // the current segment closes at the chunk end
-            if (own) csr_put<ADD>(a, r0 + row, s);
-            else { head = s; head_row = row; }
-        } else if (own) {
-            owned_tail = row;  // continues into later lanes
+        cur = fma(v, xv, cur);  // one DFMA per nonzero
+    }
+    if (nf == 0) head = cur;
+    // T_l = head_l + (lane l holds no flag ? T_{l+1} : 0)
+    double T = head;
+    int stop = nf > 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const double Tn = __shfl_down_sync(kFull, T, d);
+        const int sn = __shfl_down_sync(kFull, stop, d);
+        if (!stop && lane + d < 32) {
+            T += Tn;
+            stop = sn;
+        }
+    }
+    double next = __shfl_down_sync(kFull, T, 1);
+    if (lane == 31) next = 0.0;
+    // 4. the lane's last segment, and the joins of rows crossing tiles
+    if (first_join) csr_join<ADD>(a, r0 - 1, t, false, first);
+    if (nf > 0) {
+        const int g = yo + nf - 1;
+        const int32_t row = S.rid[g];
+        const double tot = cur + next;
+        if (g == 0 && cont) {
+            csr_join<ADD>(a, row, t, false, tot);  // continues a row begun in an earlier tile
+        } else if (g == total - 1 && (int64_t)a.ptr[row + 1] > base + kCsrW) {
+            csr_join<ADD>(a, row, t, true, tot);   // begins here, continues into later tiles
         } else {
-            head = s;  // the whole chunk lies inside a row begun earlier
-            head_row = row;
+            csr_put<ADD>(a, row, tot);
         }
     }
-    S.hv[lane] = head;
-    S.hr[lane] = head_row;
-    __syncwarp();
-    if (owned_tail >= 0) {
-        double acc = s;
-        for (int t2 = lane + 1; t2 < 32 && S.hr[t2] == owned_tail; ++t2) acc += S.hv[t2];
-        csr_put<ADD>(a, r0 + owned_tail, acc);
-    }
-    __syncwarp();
+    __syncwarp();  // the shared slice is reused by the warp's next tile
+}
+
+// y = 0 for the rows of a matrix without nonzeros (no tiles).
+__device__ __forceinline__ void csr_zero(const CsrArgs& a, int64_t i) {
+    if (i < a.rows) a.y[i] = 0.0;
 }
 
 // ------------------------------------------------------------------- ELL

@@ -9,6 +9,16 @@ block-diagonal, uniform random, power-law rows) and every step runs in the
 library: conversion, spmv_features, and spmv_run timed with CUDA events after
 an L2 flush.
 
+Each matrix is timed twice per format:
+  * "ms": one product of the matrix alone, the paper's measure (the label of
+    the selector used by spmv_select);
+  * "ms_batch": the time per copy of a product of the K-fold block-diagonal
+    replica diag(A, ..., A) (K copies, about REPLICA_NNZ nonzeros in all; K = 1
+    for larger matrices).  That product keeps the whole GPU busy with A's rows,
+    as the batched kernel does when it multiplies many matrices at once, so it
+    measures a format's throughput on A rather than the latency of a small
+    launch (the label of the selector used for batches).
+
 One JSON line per matrix is appended to the output file, so an interrupted run
 resumes where it stopped (matrices already in the file are skipped).
 
@@ -28,6 +38,29 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FORMAT_CAP_BYTES = 24 << 30  # a padded layout larger than this counts as infeasible (throughput 0)
+REPLICA_NNZ = 1 << 23        # nonzeros of the block-diagonal replica used for the throughput time
+
+
+def replica(a, k: int):
+    """diag(A, ..., A) with k copies of A (host CSR)."""
+    import numpy as np
+
+    import synth
+
+    if k == 1:
+        return a
+    off = (np.arange(k, dtype=np.int64) * a.nnz)[:, None]
+    ptr = np.concatenate([(a.ptr[:-1][None, :].astype(np.int64) + off).ravel(), [k * a.nnz]]).astype(np.int32)
+    idx = (a.idx[None, :].astype(np.int64) + (np.arange(k, dtype=np.int64) * a.n)[:, None]).ravel().astype(np.int32)
+    val = np.tile(a.val, k)
+    return synth.CSR(k * a.m, k * a.n, ptr, idx, val, f"{a.name}_x{k}")
+
+
+def replica_count(a) -> int:
+    if a.nnz == 0 or a.nnz >= REPLICA_NNZ:
+        return 1
+    k = -(-REPLICA_NNZ // a.nnz)
+    return max(1, min(k, (2**31 - 1) // max(a.n, a.m, 1) - 1))
 
 
 def done_indices(path: str) -> set:
@@ -42,16 +75,14 @@ def done_indices(path: str) -> set:
     return out
 
 
-def profile_one(a, spec, timer, cap_bytes: int, measure_kw: dict) -> dict:
-    import numpy as np
+def _time_formats(a, seed, timer, cap_bytes, measure_kw):
     import torch
 
     import synth
-    from . import FORMATS, DeviceCSR, SpmvError, spmv_convert, spmv_features, spmv_run
+    from . import FORMATS, DeviceCSR, SpmvError, spmv_convert, spmv_run
 
     d = DeviceCSR.from_host(a)
-    feat = spmv_features(d).cpu().numpy().astype(float).tolist()
-    x = torch.as_tensor(synth.vector(a.n, spec["seed"] ^ 0x77)).cuda()
+    x = torch.as_tensor(synth.vector(a.n, seed ^ 0x77)).cuda()
     y = torch.empty(a.m, dtype=torch.float64, device="cuda")
     times, status, conv = {}, {}, {}
     for f in range(5):
@@ -68,11 +99,29 @@ def profile_one(a, spec, timer, cap_bytes: int, measure_kw: dict) -> dict:
         times[FORMATS[f]] = r["ms"]
         status[FORMATS[f]] = f"ci={r['ci_halfwidth_ms'] / r['ms']:.3f} n={r['n']}"
         del h
-    feas = {k: v for k, v in times.items() if v is not None}
-    best = min(feas, key=lambda k: feas[k])
-    return {"index": spec["index"], "spec": {k: v for k, v in spec.items() if k != "seed"}, "m": a.m, "nnz": a.nnz,
+    return d, times, status, conv
+
+
+def profile_one(a, spec, timer, cap_bytes: int, measure_kw: dict) -> dict:
+    from . import FORMATS, spmv_features
+
+    d, times, status, conv = _time_formats(a, spec["seed"], timer, cap_bytes, measure_kw)
+    feat = spmv_features(d).cpu().numpy().astype(float).tolist()
+    del d
+    k = replica_count(a)
+    if k == 1:
+        times_b = dict(times)
+    else:
+        _, tb, _, _ = _time_formats(replica(a, k), spec["seed"], timer, cap_bytes, measure_kw)
+        times_b = {f: (None if v is None else v / k) for f, v in tb.items()}
+    feas = {f: v for f, v in times.items() if v is not None}
+    best = min(feas, key=lambda f: feas[f])
+    feas_b = {f: v for f, v in times_b.items() if v is not None}
+    best_b = min(feas_b, key=lambda f: feas_b[f])
+    return {"index": spec["index"], "spec": {k2: v for k2, v in spec.items() if k2 != "seed"}, "m": a.m, "nnz": a.nnz,
             "features": feat, "ms": times, "status": status, "convert_ms": conv, "label": FORMATS.index(best),
-            "best": best}
+            "best": best, "replicas": k, "ms_batch": times_b, "label_batch": FORMATS.index(best_b),
+            "best_batch": best_b}
 
 
 def run(out: str, count: int = 1000, start: int = 0, cap_bytes: int = FORMAT_CAP_BYTES, n_min: int = 10,
@@ -98,7 +147,7 @@ def run(out: str, count: int = 1000, start: int = 0, cap_bytes: int = FORMAT_CAP
             fh.flush()
             if j % 50 == 0:
                 log(f"[{j + 1}/{len(todo)}] matrix {i} {rec['spec']['family']} n={a.m} nnz={a.nnz} best={rec['best']} "
-                    f"({time.time() - t_start:.0f} s)")
+                    f"batch best={rec['best_batch']} ({time.time() - t_start:.0f} s)", flush=True)
 
 
 def main():

@@ -11,7 +11,12 @@ full-batch Adam training loop (spmv_mlp_train) and inference
 (spmv_mlp_forward) all run in this library's CUDA kernels.  The split is 800
 training / 200 held-out matrices by a seeded shuffle.
 
-    python -m paper_1805_11938_gb300.train_selector --table table.jsonl --out model.json
+Two models come from one profiling table: --key ms learns the fastest format
+for one product of a matrix alone (spmv_select's model), --key ms_batch the
+format with the best throughput when the GPU is kept busy, as in a batch
+(the model that picks formats for spmv_batch).
+
+    python -m paper_1805_11938_gb300.train_selector --table table.jsonl --out model.json [--key ms_batch]
 """
 from __future__ import annotations
 
@@ -81,13 +86,16 @@ def _dev(a, dtype=None):
     return torch.as_tensor(np.ascontiguousarray(a)).cuda() if dtype is None else torch.as_tensor(np.ascontiguousarray(a, dtype=dtype)).cuda()
 
 
-def fit(records: list, train_idx, steps: int = 3000, lr: float = 3e-3, seed: int = 1) -> dict:
+LABEL_OF = {"ms": "label", "ms_batch": "label_batch"}
+
+
+def fit(records: list, train_idx, steps: int = 3000, lr: float = 3e-3, seed: int = 1, key: str = "ms") -> dict:
     import torch
 
     from . import spmv_mlp_scale, spmv_mlp_train
 
     F = np.array([records[i]["features"] for i in train_idx], dtype=np.float32)
-    labels = np.array([records[i]["label"] for i in train_idx], dtype=np.int32)
+    labels = np.array([records[i][LABEL_OF[key]] for i in train_idx], dtype=np.int32)
     t = transform(F.astype(np.float64))
     lo, hi = t.min(axis=0).astype(np.float32), t.max(axis=0).astype(np.float32)
     X = spmv_mlp_scale(_dev(F), _dev(lo), _dev(hi))
@@ -108,23 +116,23 @@ def predict(model: dict, records: list, idx) -> np.ndarray:
     return pred.cpu().numpy()
 
 
-def pct_of_best(records: list, idx, choice) -> np.ndarray:
+def pct_of_best(records: list, idx, choice, key: str = "ms") -> np.ndarray:
     """perf(chosen) / perf(best) = t_best / t_chosen per matrix (0 if the chosen format is infeasible)."""
     out = []
     for i, c in zip(idx, choice):
-        ms = records[i]["ms"]
+        ms = records[i][key]
         best = min(v for v in ms.values() if v is not None)
         t = ms[FORMATS[int(c)]]
         out.append(0.0 if t is None else best / t)
     return np.array(out)
 
 
-def summary(records: list, idx, pred) -> dict:
-    r = pct_of_best(records, idx, pred)
+def summary(records: list, idx, pred, key: str = "ms") -> dict:
+    r = pct_of_best(records, idx, pred, key)
     out = {"mean_pct_of_best": 100 * float(r.mean()), "geomean_pct_of_best": 100 * float(np.exp(np.log(np.maximum(r, 1e-9)).mean())),
            "worst_pct_of_best": 100 * float(r.min()),
-           "accuracy": float(np.mean([records[i]["label"] == int(p) for i, p in zip(idx, pred)])), "n": len(idx)}
-    fixed = {FORMATS[f]: 100 * float(pct_of_best(records, idx, [f] * len(idx)).mean()) for f in range(5)}
+           "accuracy": float(np.mean([records[i][LABEL_OF[key]] == int(p) for i, p in zip(idx, pred)])), "n": len(idx)}
+    fixed = {FORMATS[f]: 100 * float(pct_of_best(records, idx, [f] * len(idx), key).mean()) for f in range(5)}
     out["fixed_format_mean_pct_of_best"] = fixed
     out["best_fixed_format"] = max(fixed, key=fixed.get)
     out["gain_over_best_fixed_pct_points"] = out["mean_pct_of_best"] - fixed[out["best_fixed_format"]]
@@ -139,15 +147,17 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--key", default="ms", choices=sorted(LABEL_OF))
     args = ap.parse_args()
     recs = load_table(args.table)
     assert [r["index"] for r in recs] == list(range(len(recs))), "table must hold matrices 0..n-1"
     tr, te = split(len(recs), n_train=int(round(0.8 * len(recs))))
-    model = fit(recs, tr, args.steps, args.lr, args.seed)
-    ev_train = summary(recs, tr, predict(model, recs, tr))
-    ev_test = summary(recs, te, predict(model, recs, te))
+    model = fit(recs, tr, args.steps, args.lr, args.seed, args.key)
+    ev_train = summary(recs, tr, predict(model, recs, tr), args.key)
+    ev_test = summary(recs, te, predict(model, recs, te), args.key)
     out = {"params": model["params"].tolist(), "lo": model["lo"].tolist(), "hi": model["hi"].tolist(),
            "features": "spmv_features v1 (16 features, rows sampled above 16384)",
+           "timing": args.key,
            "training": {k: model[k] for k in ("steps", "lr", "seed", "loss_first", "loss_last")},
            "n_train": len(tr), "n_test": len(te), "train": ev_train, "held_out": ev_test}
     with open(args.out, "w") as f:

@@ -157,18 +157,19 @@ def test_select_without_model():
     assert ei.value.name == "NO_MODEL"
 
 
-def test_committed_model_on_corpus_matrices():
-    """spmv_select with the shipped model picks, on regenerated corpus matrices, what the
+@pytest.mark.parametrize("name", ["selector_mlp.json", "selector_mlp_batch.json"])
+def test_committed_model_on_corpus_matrices(name):
+    """spmv_select with a shipped model picks, on regenerated corpus matrices, what the
     oracle's network picks from the features stored when the table was profiled."""
     import json
     import os
 
     data = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1805_11938_gb300", "data")
-    with open(os.path.join(data, "selector_mlp.json")) as f:
+    with open(os.path.join(data, name)) as f:
         md = json.load(f)
     with open(os.path.join(data, "corpus_table.jsonl")) as f:
         recs = {json.loads(l)["index"]: json.loads(l) for l in f}
-    model = sp.Model.load(os.path.join(data, "selector_mlp.json"))
+    model = sp.Model.load(os.path.join(data, name))
     theta = np.array(md["params"], np.float64)
     lo, hi = np.array(md["lo"], np.float64), np.array(md["hi"], np.float64)
     small = [i for i in sorted(recs) if recs[i]["nnz"] < 2_000_000][:12]

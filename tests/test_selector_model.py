@@ -1,12 +1,17 @@
-"""What the trained selector gains over the method without it (CPU).
+"""What the trained selectors gain over the method without them (CPU).
 
 Uses the committed profiling table (every corpus matrix timed in all five
-formats on the GB300 by the library itself) and the committed network.  The
+formats on the GB300 by the library itself) and the committed networks.  The
 oracle's FP64 network predicts the held-out matrices from their stored
 features; the result is scored with the paper's measure (Sec. V-C):
 performance of the predicted format relative to the exhaustively best one.
 Without the network the choice is one fixed format for every matrix
 (Table III's setting) or always CSR.
+
+Two models are checked against their own timings: selector_mlp.json against
+"ms" (one product of the matrix alone) and selector_mlp_batch.json against
+"ms_batch" (throughput per copy of a block-diagonal replica, the regime of the
+batched kernel).
 """
 import json
 import os
@@ -28,9 +33,16 @@ def table():
     return recs
 
 
-@pytest.fixture(scope="module")
-def model():
-    with open(os.path.join(DATA, "selector_mlp.json")) as f:
+MODELS = {"ms": "selector_mlp.json", "ms_batch": "selector_mlp_batch.json"}
+# required gain over the best single format: in the throughput regime the best
+# fixed format (SELL or HYB) is already within about 10 % of the exhaustive best
+MARGIN = {"ms": 0.10, "ms_batch": 0.05}
+LABEL = {"ms": "label", "ms_batch": "label_batch"}
+BEST = {"ms": "best", "ms_batch": "best_batch"}
+
+
+def _model(key):
+    with open(os.path.join(DATA, MODELS[key])) as f:
         return json.load(f)
 
 
@@ -42,11 +54,11 @@ def _split(n):
     return np.sort(order[:800]), np.sort(order[800:])
 
 
-def _pct(recs, idx, choice):
+def _pct(recs, idx, choice, key="ms"):
     out = []
     for i, c in zip(idx, choice):
-        best = min(v for v in recs[i]["ms"].values() if v is not None)
-        t = recs[i]["ms"][FORMATS[int(c)]]
+        best = min(v for v in recs[i][key].values() if v is not None)
+        t = recs[i][key][FORMATS[int(c)]]
         out.append(0.0 if t is None else best / t)
     return np.array(out)
 
@@ -57,29 +69,37 @@ def _predict(model, F):
     return mlp.predict(np.array(model["params"], np.float64), x)
 
 
-def test_table_labels_are_the_fastest_format(table):
+@pytest.mark.parametrize("key", sorted(MODELS))
+def test_table_labels_are_the_fastest_format(table, key):
     for r in table:
-        feas = {k: v for k, v in r["ms"].items() if v is not None}
-        assert r["best"] == min(feas, key=feas.get) and FORMATS[r["label"]] == r["best"]
+        feas = {k: v for k, v in r[key].items() if v is not None}
+        assert r[BEST[key]] == min(feas, key=feas.get) and FORMATS[r[LABEL[key]]] == r[BEST[key]]
         assert len(r["features"]) == 16
+        if r["replicas"] == 1:
+            assert r["ms_batch"] == r["ms"]  # no replica: the throughput time is the single-product time
 
 
-def test_scaling_table_is_training_minmax(table, model):
+@pytest.mark.parametrize("key", sorted(MODELS))
+def test_scaling_table_is_training_minmax(table, key):
+    model = _model(key)
+    assert model["timing"] == key
     tr, _ = _split(len(table))
     t = mlp.transform(np.array([table[i]["features"] for i in tr], np.float64))
     assert np.allclose(model["lo"], t.min(axis=0), rtol=1e-6, atol=1e-6)
     assert np.allclose(model["hi"], t.max(axis=0), rtol=1e-6, atol=1e-6)
 
 
-def test_selector_beats_every_fixed_format_on_held_out(table, model):
+@pytest.mark.parametrize("key", sorted(MODELS))
+def test_selector_beats_every_fixed_format_on_held_out(table, key):
+    model = _model(key)
     _, te = _split(len(table))
     F = np.array([table[i]["features"] for i in te])
     pred = _predict(model, F)
-    mine = _pct(table, te, pred)
-    fixed = {f: _pct(table, te, [k] * len(te)).mean() for k, f in enumerate(FORMATS)}
+    mine = _pct(table, te, pred, key)
+    fixed = {f: _pct(table, te, [k] * len(te), key).mean() for k, f in enumerate(FORMATS)}
     best_fixed = max(fixed.values())
     assert mine.mean() >= 0.95  # the 95%-of-best target
-    assert mine.mean() >= best_fixed + 0.10  # at least ten points over the best single format
+    assert mine.mean() >= best_fixed + MARGIN[key]  # over the best single format
     assert mine.mean() >= fixed["CSR"] + 0.10  # and over "always CSR"
     # the stored evaluation (made on the GPU by the library's kernels) agrees with the oracle's
     assert abs(100 * mine.mean() - model["held_out"]["mean_pct_of_best"]) < 1.0
