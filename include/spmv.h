@@ -85,7 +85,7 @@ typedef struct {
                               or -1 for the whole matrix (0 -> the whole matrix) */
     int32_t csr5_omega;    /* CSR5 tile width: 32, the warp width, is the only value (0 -> 32) */
     int32_t csr5_sigma;    /* CSR5 tile height, 1..32 (0 -> 32) */
-    int32_t csr_block_nnz; /* CSR warp-unit nonzero budget: 0 or 416, the only value (0 -> 416) */
+    int32_t csr_block_nnz; /* CSR nonzeros per warp tile: 0 or 352, the only value (0 -> 352) */
     int32_t hyb_k;         /* HYB ELL width: > 0 explicit, 0 -> the typical-length rule,
                               SPMV_HYB_K_NONE -> every entry in the COO part */
     int64_t max_bytes;     /* cap on the handle's device footprint (0 -> 90% of free memory) */

@@ -73,11 +73,14 @@ __device__ __forceinline__ double block_sum256(double v, double* red) {
 //  3. lane l walks its kCsrCT nonzeros with one gather and one DFMA each,
 //     writing every row that begins and ends in its chunk; a segmented
 //     suffix sum over the lanes (shuffles) completes the rows spanning lanes;
-//  4. a row that crosses tile boundaries is finished by the last of its tiles
-//     to arrive: each stores its part in a per-tile slot and takes a ticket,
-//     and the last ticket holder adds the slots in tile order (no waiting,
-//     deterministic order).
-constexpr int kCsrCT = 13;          // nonzeros per lane (odd: conflict-free shared accesses)
+//  4. a tile owns the rows that begin in it.  When its last row runs past
+//     the tile end by at most W nonzeros, the warp reads that overflow itself
+//     (coalesced, one warp reduction) and the next tile skips the row's head
+//     without gathering it.  A longer row is finished by the last of its
+//     tiles to arrive: each stores its part in a per-tile slot and takes a
+//     ticket, and the last ticket holder adds the slots in tile order (no
+//     waiting, deterministic order).
+constexpr int kCsrCT = 11;          // nonzeros per lane (odd: conflict-free shared accesses)
 constexpr int kCsrW = 32 * kCsrCT;  // nonzeros per tile
 
 struct CsrArgs {
@@ -157,7 +160,16 @@ __device__ __forceinline__ void csr_tile(const CsrArgs& a, int32_t t, CsrWarpSme
     S.fl[lane] = lane == 0 ? 1u : 0u;  // the tile's first nonzero always opens a segment
     __syncwarp();
     // 2. the rows starting in the tile
-    const bool cont = a.ptr[r0] > base;  // nonzero `base` lies in row r0 - 1, begun earlier
+    const int32_t p_r0 = a.ptr[r0];
+    const int32_t p_r1 = a.ptr[r1];      // end of the tile's last row
+    const bool cont = p_r0 > base;       // nonzero `base` lies in row r0 - 1, begun earlier
+    // that row is finished by the tile it began in when it overflows that tile by <= W
+    bool skip_head = false;
+    if (cont) {
+        const int64_t ts = a.ptr[r0 - 1] / kCsrW;
+        skip_head = (int64_t)p_r0 - (ts + 1) * kCsrW <= kCsrW;
+    }
+    const int32_t head_end = (int32_t)((int64_t)p_r0 - base);  // tile position after that row
     if (cont && lane == 0) S.rid[0] = r0 - 1;
     int32_t nseg = cont ? 1 : 0;
     for (int32_t rb = r0; rb < r1; rb += 32) {
@@ -197,7 +209,7 @@ __device__ __forceinline__ void csr_tile(const CsrArgs& a, int32_t t, CsrWarpSme
 #pragma unroll
     for (int r = 0; r < kCsrCT; ++r) {
         const int k = c0 + r;
-        const bool valid = k < n;  // false only in the last, partial tile
+        const bool valid = k < n && !(skip_head && k < head_end);  // past the end, or another tile's row
         const double v = valid ? S.sv[k] : 0.0;
         const double xv = valid ? ldx(a.x, S.si[k]) : 0.0;
         if ((f >> r) & 1u) {
@@ -232,16 +244,24 @@ __device__ __forceinline__ void csr_tile(const CsrArgs& a, int32_t t, CsrWarpSme
     }
     double next = __shfl_down_sync(kFull, T, 1);
     if (lane == 31) next = 0.0;
-    // 4. the lane's last segment, and the joins of rows crossing tiles
-    if (first_join) csr_join<ADD>(a, r0 - 1, t, false, first);
+    // 4. the lane's last segment, and the rows crossing tiles
+    const bool crosses = (int64_t)p_r1 > base + kCsrW && !(total == 1 && cont);  // a row begun here runs on
+    const bool own_overflow = crosses && (int64_t)p_r1 - (base + kCsrW) <= kCsrW;  // warp-uniform
+    double ov = 0.0;
+    if (own_overflow) {
+        for (int64_t k = base + kCsrW + lane; k < p_r1; k += 32) ov = fma(__ldcs(a.val + k), ldx(a.x, __ldcs(a.idx + k)), ov);
+        ov = warp_sum(ov);
+    }
+    if (first_join && !skip_head) csr_join<ADD>(a, r0 - 1, t, false, first);
     if (nf > 0) {
         const int g = yo + nf - 1;
         const int32_t row = S.rid[g];
         const double tot = cur + next;
-        if (g == 0 && cont) {
-            csr_join<ADD>(a, row, t, false, tot);  // continues a row begun in an earlier tile
-        } else if (g == total - 1 && (int64_t)a.ptr[row + 1] > base + kCsrW) {
-            csr_join<ADD>(a, row, t, true, tot);   // begins here, continues into later tiles
+        if (g == 0 && cont) {  // continues a row begun in an earlier tile
+            if (!skip_head) csr_join<ADD>(a, row, t, false, tot);
+        } else if (g == total - 1 && crosses) {  // begins here, continues into later tiles
+            if (own_overflow) csr_put<ADD>(a, row, tot + ov);
+            else csr_join<ADD>(a, row, t, true, tot);
         } else {
             csr_put<ADD>(a, row, tot);
         }

@@ -51,10 +51,11 @@ def matrices_small():
     lens = np.zeros(64, np.int32)
     lens[31] = 60_000
     out.append(synth.from_lengths_random_cols(lens, 60_000, 110, "one_long_row"))
-    # rows starting on 416-nonzero boundaries, spanning two and three of them, empty rows around
-    lens = np.array([0, 416, 416, 415, 1, 417, 832, 1, 0, 0, 0], dtype=np.int32)
+    # CSR tiles hold 352 nonzeros: rows starting on tile boundaries, spanning two and three
+    # tiles, overflowing the next tile by exactly one tile and by one more, empty rows around
+    lens = np.array([0, 352, 352, 351, 1, 353, 704, 1, 0, 351, 353, 351, 354, 0, 0], dtype=np.int32)
     out.append(synth.from_lengths_random_cols(lens, 900, 111, "tile_edges"))
-    # nonzeros an exact multiple of 416, trailing empty rows
-    lens = np.array([0, 0, 416, 0, 416, 0, 0], dtype=np.int32)
+    # nonzeros an exact multiple of 352, trailing empty rows
+    lens = np.array([0, 0, 352, 0, 352, 0, 0], dtype=np.int32)
     out.append(synth.from_lengths_random_cols(lens, 500, 112, "tile_exact"))
     return out

@@ -31,7 +31,7 @@ def _lib():
 
 MATS = matrices_small()
 PARAMS = {
-    0: [None, {"csr_block_nnz": 416}],
+    0: [None, {"csr_block_nnz": 352}],
     1: [None, {"csr5_sigma": 1}, {"csr5_sigma": 4}, {"csr5_sigma": 32}],
     2: [None],
     3: [None, {"sell_C": 64, "sell_sigma": 1}, {"sell_C": 128, "sell_sigma": -1}, {"sell_C": 32, "sell_sigma": 256}],
