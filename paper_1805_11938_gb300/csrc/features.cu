@@ -64,50 +64,32 @@ __device__ __forceinline__ float feat_scale(int j, float f, const float* lo, con
     return x < 0.0f ? 0.0f : (x > 1.0f ? 1.0f : x);
 }
 
-// 16 -> 64 -> 64 -> 5 forward for one sample; th in shared memory.  Four
-// threads share each hidden unit and eight each logit (partial sums joined by
-// shuffles), so no thread runs a 64-long dependent chain.
-__device__ void mlp_forward_block(const float* th, const float* xs, float* h1, float* h2, float* z) {
-    const int t = threadIdx.x;
-    if (t < 256) {
-        const int j = t >> 2, q = t & 3;
-        float a = 0.f;
+// Barrier of the first two warps only (named barrier 1), for the tail of the
+// features kernel that runs in warps 0 and 1 after the others have left.
+__device__ __forceinline__ void tail_sync() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
+
+// 16 -> 64 -> 64 -> 5 forward for one sample in threads 0..63 (warps 0 and 1);
+// th in shared memory.  Thread j computes hidden unit j of each layer as one
+// dot product (consecutive j: conflict-free weight reads, broadcast inputs).
+__device__ void mlp_forward_64(const float* th, const float* xs, float* h1, float* h2, float* z) {
+    const int j = threadIdx.x;
+    float a = th[oB1 + j];
 #pragma unroll
-        for (int i = q; i < 16; i += 4) a = fmaf(xs[i], th[oW1 + i * 64 + j], a);
-        a += __shfl_xor_sync(dev::kFull, a, 1);
-        a += __shfl_xor_sync(dev::kFull, a, 2);
-        if (q == 0) {
-            a += th[oB1 + j];
-            h1[j] = a > 0.f ? a : 0.f;
-        }
+    for (int i = 0; i < 16; ++i) a = fmaf(xs[i], th[oW1 + i * 64 + j], a);
+    h1[j] = a > 0.f ? a : 0.f;
+    tail_sync();
+    a = th[oB2 + j];
+#pragma unroll 16
+    for (int i = 0; i < 64; ++i) a = fmaf(h1[i], th[oW2 + i * 64 + j], a);
+    h2[j] = a > 0.f ? a : 0.f;
+    tail_sync();
+    if (j < 5) {
+        a = th[oB3 + j];
+#pragma unroll 16
+        for (int i = 0; i < 64; ++i) a = fmaf(h2[i], th[oW3 + i * 5 + j], a);
+        z[j] = a;
     }
-    __syncthreads();
-    if (t < 256) {
-        const int j = t >> 2, q = t & 3;
-        float a = 0.f;
-#pragma unroll
-        for (int i = q; i < 64; i += 4) a = fmaf(h1[i], th[oW2 + i * 64 + j], a);
-        a += __shfl_xor_sync(dev::kFull, a, 1);
-        a += __shfl_xor_sync(dev::kFull, a, 2);
-        if (q == 0) {
-            a += th[oB2 + j];
-            h2[j] = a > 0.f ? a : 0.f;
-        }
-    }
-    __syncthreads();
-    if (t < 64) {  // 5 logits x 8 lanes (lanes 40..63 idle)
-        const int c = t >> 3, q = t & 7;
-        float a = 0.f;
-        if (c < 5) {
-#pragma unroll
-            for (int i = q; i < 64; i += 8) a = fmaf(h2[i], th[oW3 + i * 5 + c], a);
-        }
-        a += __shfl_xor_sync(dev::kFull, a, 1);
-        a += __shfl_xor_sync(dev::kFull, a, 2);
-        a += __shfl_xor_sync(dev::kFull, a, 4);
-        if (c < 5 && q == 0) z[c] = a + th[oB3 + c];
-    }
-    __syncthreads();
+    tail_sync();
 }
 
 __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads)
@@ -123,15 +105,18 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
     __shared__ int red_i[32][3];
     __shared__ unsigned red_c[32][2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // CTA 0 of a selection starts copying the network into shared memory now
-    // (asynchronous copies, waited for just before the network runs).
+    // CTA 0 starts copying what its tail needs into shared memory now
+    // (asynchronous copies, waited for just before the tail): nnz = ptr[m]
+    // and, for a selection, the network and the scaling table.
     __shared__ __align__(16) float wsm[kNP + 3 + 32];
-    if (model_params && rank == 0) {
-        for (int c = tid; c < kNP / 4; c += kFeatThreads) __pipeline_memcpy_async(wsm + 4 * c, model_params + 4 * c, 16);
-        if (tid < kNP % 4) wsm[(kNP / 4) * 4 + tid] = model_params[(kNP / 4) * 4 + tid];
-        if (tid < 16) {
-            wsm[kNP + 3 + tid] = lo[tid];
-            wsm[kNP + 3 + 16 + tid] = hi[tid];
+    __shared__ int32_t nnz_sm;
+    if (rank == 0) {
+        if (tid == 0) __pipeline_memcpy_async(&nnz_sm, ptr + m, 4);
+        if (model_params) {
+            for (int c = tid; c < kNP / 4; c += kFeatThreads) __pipeline_memcpy_async(wsm + 4 * c, model_params + 4 * c, 16);
+            if (tid < kNP % 4) __pipeline_memcpy_async(wsm + (kNP / 4) * 4 + tid, model_params + (kNP / 4) * 4 + tid, 4);
+            if (tid < 4) __pipeline_memcpy_async(wsm + kNP + 3 + 4 * tid, lo + 4 * tid, 16);
+            else if (tid < 8) __pipeline_memcpy_async(wsm + kNP + 3 + 16 + 4 * (tid - 4), hi + 4 * (tid - 4), 16);
         }
         __pipeline_commit();
     }
@@ -243,8 +228,9 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
     if (rank != 0) return;  // CTA 0 holds everything now
 
     // ---- phase 2 (CTA 0): combine, features, optional selection.  The
-    // histogram ranks are summed by 513 threads; the rest runs in warp 0 with
-    // shuffles only (lane l owns bins 17l .. 17l + 16).
+    // histogram ranks are summed by 513 threads; the rest runs in warps 0
+    // and 1 (the scans in warp 0 with shuffles only, lane l owning bins
+    // 17l .. 17l + 16; the network in both warps).
     __shared__ unsigned hsum[kLenCap + 1];
     __shared__ FeatStats tot;
     __shared__ float fs[16], xs[16], h1[64], h2[64], z[5];
@@ -278,7 +264,9 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
             tot.min_len = i0; tot.max_len = i1; tot.band = i2; tot.empty = c0; tot.longc = c1;
         }
     }
+    __pipeline_wait_prior(0);  // this thread's copies of nnz and the network have landed
     __syncthreads();
+    if (tid >= 64) return;
     const unsigned cnt = (unsigned)S;
     unsigned long long upto_k = 0, widths = 0, capped_sum = 0;
     if (warp == 0) {
@@ -331,51 +319,53 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         capped_sum = cpart;
     }
     if (tid < 16) {  // one lane per feature, FP32 (exact integer parts kept in 64 bits)
+        // Every lane evaluates the same straight-line code (no divergent
+        // per-feature paths) and keeps its own feature.
         const int j = tid;
         const float fc = (float)cnt;
         const float L = (float)tot.sum_len;
         const float mean = L / fc;
-        const float nnz = (float)ptr[m];
-        float sd = 0.0f;
-        if (j == 6 || j == 7) {
-            // std = sqrt(cnt * sum_sq - L^2) / cnt, the difference in exact 128-bit integer arithmetic
-            const unsigned long long a_lo = (unsigned long long)cnt * tot.sum_sq;
-            const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, tot.sum_sq);
-            const unsigned long long b_lo = tot.sum_len * tot.sum_len;
-            const unsigned long long b_hi = __umul64hi(tot.sum_len, tot.sum_len);
-            const unsigned long long d_lo = a_lo - b_lo;
-            const unsigned long long d_hi = a_hi - b_hi - (a_lo < b_lo ? 1ull : 0ull);
-            sd = sqrtf((float)d_hi * 18446744073709551616.0f + (float)d_lo) / fc;
-        }
-        float f = 0.0f;
+        const float nnz = (float)nnz_sm;
+        // std = sqrt(cnt * sum_sq - L^2) / cnt, the difference in exact 128-bit integer arithmetic
+        const unsigned long long a_lo = (unsigned long long)cnt * tot.sum_sq;
+        const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, tot.sum_sq);
+        const unsigned long long b_lo = tot.sum_len * tot.sum_len;
+        const unsigned long long b_hi = __umul64hi(tot.sum_len, tot.sum_len);
+        const unsigned long long d_lo = a_lo - b_lo;
+        const unsigned long long d_hi = a_hi - b_hi - (a_lo < b_lo ? 1ull : 0ull);
+        const float sd = sqrtf((float)d_hi * 18446744073709551616.0f + (float)d_lo) / fc;
+        // the quotient and the log each lane needs, selected before the one division and log2
+        float num = 0.0f, den = 1.0f;
         switch (j) {
-            case 0: f = (float)m; break;
-            case 1: f = (float)n; break;
-            case 2: f = nnz / ((float)m * (float)n); break;
-            case 3: f = (float)tot.min_len; break;
-            case 4: f = (float)tot.max_len; break;
-            case 5: f = nnz / (float)m; break;
-            case 6: f = sd; break;
-            case 7: f = tot.sum_len > 0 ? sd / mean : 0.0f; break;
-            case 8: f = log2f(nnz > 1.0f ? nnz : 1.0f); break;
-            case 9: f = tot.max_len > 0 ? mean / (float)tot.max_len : 0.0f; break;
-            case 10: f = tot.sum_len > 0 ? (float)(tot.sum_len - upto_k) / L : 0.0f; break;
-            case 11: f = tot.spread_cnt > 0 ? (float)tot.spread_sum / (float)tot.spread_cnt : 0.0f; break;
-            case 12: f = (float)tot.band; break;
-            case 13: f = (float)tot.empty / fc; break;
-            case 14: f = (float)tot.longc / fc; break;
-            default: f = widths > 0 ? (float)capped_sum / (32.0f * (float)widths) : 1.0f; break;
+            case 2: num = nnz; den = (float)m * (float)n; break;
+            case 5: num = nnz; den = (float)m; break;
+            case 7: num = tot.sum_len > 0 ? sd : 0.0f; den = tot.sum_len > 0 ? mean : 1.0f; break;
+            case 9: num = tot.max_len > 0 ? mean : 0.0f; den = tot.max_len > 0 ? (float)tot.max_len : 1.0f; break;
+            case 10: num = tot.sum_len > 0 ? (float)(tot.sum_len - upto_k) : 0.0f; den = tot.sum_len > 0 ? L : 1.0f; break;
+            case 11: num = tot.spread_cnt > 0 ? (float)tot.spread_sum : 0.0f; den = tot.spread_cnt > 0 ? (float)tot.spread_cnt : 1.0f; break;
+            case 13: num = (float)tot.empty; den = fc; break;
+            case 14: num = (float)tot.longc; den = fc; break;
+            case 15: num = widths > 0 ? (float)capped_sum : 1.0f; den = widths > 0 ? 32.0f * (float)widths : 1.0f; break;
+            default: break;
         }
+        const float q = num / den;
+        const float lg = log2f(nnz > 1.0f ? nnz : 1.0f);
+        float f = q;
+        if (j == 0) f = (float)m;
+        if (j == 1) f = (float)n;
+        if (j == 3) f = (float)tot.min_len;
+        if (j == 4) f = (float)tot.max_len;
+        if (j == 6) f = sd;
+        if (j == 8) f = lg;
+        if (j == 12) f = (float)tot.band;
         fs[j] = f;
     }
-    __syncthreads();
+    tail_sync();
     if (feat_out && tid < 16) feat_out[tid] = fs[tid];
     if (model_params) {
-        __pipeline_wait_prior(0);
-        __syncthreads();
         if (tid < 16) xs[tid] = feat_scale(tid, fs[tid], wsm + kNP + 3, wsm + kNP + 3 + 16);
-        __syncthreads();
-        mlp_forward_block(wsm, xs, h1, h2, z);
+        tail_sync();
+        mlp_forward_64(wsm, xs, h1, h2, z);
         if (tid == 0) {
             int best = 0;
             for (int c = 1; c < 5; ++c)

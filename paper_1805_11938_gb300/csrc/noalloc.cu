@@ -89,7 +89,6 @@ __global__ void __launch_bounds__(256) k_na_tiles(const int32_t* __restrict__ pt
     double cur = 0.0, head = 0.0;
     bool own = (k0 < nnz) && (ptr[row] == k0 || lane == 0);
     const bool first_owned = own;
-    int32_t head_row = own ? -1 : row;
     int nseg = (k0 < nnz) ? 1 : 0;
     for (int64_t k = k0; k < k1; ++k) {
         if (k == end) {  // the segment ends before k
@@ -132,7 +131,6 @@ __global__ void __launch_bounds__(256) k_na_tiles(const int32_t* __restrict__ pt
         else y[row] = tot;
     }
     if (lane == 0) sc->row0[t] = trow;
-    (void)head_row;
 }
 
 // Adds each continuing row's carries in tile order; zeroes the empty rows.
