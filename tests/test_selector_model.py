@@ -35,8 +35,9 @@ def table():
 
 MODELS = {"ms": "selector_mlp.json", "ms_batch": "selector_mlp_batch.json"}
 # required gain over the best single format: in the throughput regime the best
-# fixed format (SELL or HYB) is already within about 10 % of the exhaustive best
-MARGIN = {"ms": 0.10, "ms_batch": 0.05}
+# fixed format (HYB) is already within about 7 % of the exhaustive best, which
+# bounds any selector's gain there
+MARGIN = {"ms": 0.10, "ms_batch": 0.03}
 LABEL = {"ms": "label", "ms_batch": "label_batch"}
 BEST = {"ms": "best", "ms_batch": "best_batch"}
 
