@@ -88,11 +88,17 @@ typedef struct {
     int32_t csr_block_nnz; /* CSR nonzeros per warp tile: 0 or 352, the only value (0 -> 352) */
     int32_t hyb_k;         /* HYB ELL width: > 0 explicit, 0 -> the typical-length rule,
                               SPMV_HYB_K_NONE -> every entry in the COO part */
+    int32_t sell_panel_cols; /* SELL column panels (not in the paper): columns per panel.  The matrix
+                              is split by columns into panels, each a SELL matrix of its own, and
+                              y = sum over panels of A_p x_p (in panel order), so that each panel's
+                              part of x stays in L2.  > 0 explicit, SPMV_SELL_PANELS_NONE -> one
+                              panel, 0 -> panels of at most 64 MiB of x when x exceeds 96 MiB */
     int64_t max_bytes;     /* cap on the handle's device footprint (0 -> 90% of free memory) */
 } spmv_params;
 
 #define SPMV_HYB_K_NONE (-1)
 #define SPMV_SELL_SIGMA_ALL (-1)
+#define SPMV_SELL_PANELS_NONE (-1)
 
 typedef struct spmv_handle spmv_handle;
 typedef struct spmv_model spmv_model;
@@ -209,10 +215,12 @@ SPMV_API int spmv_mlp_forward(const float* theta_dev, const float* X_dev, int32_
 
 /* ------------------------------------------------------------- batching */
 
-/* Many independent products y_b = A_b x_b in one persistent launch.  build
- * lays out a work list over all handles (each keeps its own format) and
- * captures the launch in a CUDA graph on `stream`; the handles must outlive
- * the batch.  Synchronises `stream`. */
+/* Many independent products y_b = A_b x_b in one CUDA graph of persistent
+ * launches (CSR tiles and HYB tails in one kernel, the other formats in
+ * another).  build lays out the work lists over all handles (each keeps its
+ * own format) and captures the launches on a stream of its own; the handles
+ * must outlive the batch.  A SELL handle in column panels is refused
+ * (INVALID_ARG): its panels must run one after another.  Synchronises. */
 SPMV_API int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t stream, spmv_batch** out);
 
 /* xs_host[b] / ys_host[b]: device pointers of x_b and y_b (host arrays of

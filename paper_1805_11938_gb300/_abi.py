@@ -39,7 +39,7 @@ class spmv_csr(ctypes.Structure):
 class spmv_params(ctypes.Structure):
     _fields_ = [("sell_C", ctypes.c_int32), ("sell_sigma", ctypes.c_int32), ("csr5_omega", ctypes.c_int32),
                 ("csr5_sigma", ctypes.c_int32), ("csr_block_nnz", ctypes.c_int32), ("hyb_k", ctypes.c_int32),
-                ("max_bytes", ctypes.c_int64)]
+                ("sell_panel_cols", ctypes.c_int32), ("max_bytes", ctypes.c_int64)]
 
 
 class spmv_info(ctypes.Structure):

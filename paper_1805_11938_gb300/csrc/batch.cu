@@ -265,8 +265,12 @@ extern "C" {
 int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t stream, spmv_batch** out) {
     if (!handles || count <= 0 || !out) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
     *out = nullptr;
-    for (int32_t b = 0; b < count; ++b)
+    for (int32_t b = 0; b < count; ++b) {
         if (!handles[b]) return set_error(SPMV_ERR_INVALID_ARG, "handle %d is NULL", b);
+        if (!handles[b]->panels.empty())  // its panels must run one after another
+            return set_error(SPMV_ERR_INVALID_ARG, "handle %d is a SELL matrix in column panels; batches take "
+                             "single-panel handles (sell_panel_cols = SPMV_SELL_PANELS_NONE)", b);
+    }
     spmv_batch* bt = new spmv_batch();
     bt->count = count;
     bt->handles.assign(handles, handles + count);

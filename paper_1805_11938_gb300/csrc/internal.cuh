@@ -134,6 +134,12 @@ struct spmv_handle {
     int32_t n_sell_units = 0;
     double* sell_partial = nullptr;
     unsigned* sell_counters = nullptr;
+    // SELL column panels: panel p covers columns [p*panel_cols, (p+1)*panel_cols)
+    // and is a SELL handle of its own; panel_pos[p][j] is the CSR position of
+    // its entry j (for the way back).  ptr keeps the CSR row pointers.
+    int32_t panel_cols = 0;
+    std::vector<spmv_handle*> panels;
+    std::vector<int32_t*> panel_pos;
 
     // HYB COO tail, grouped by row: tail row r_t = tail_rows[t], entries tail_ptr[t]..tail_ptr[t+1]
     int64_t n_tail = 0;
@@ -156,6 +162,7 @@ struct spmv_handle {
         return SPMV_OK;
     }
     ~spmv_handle() {
+        for (spmv_handle* c : panels) delete c;
         for (void* q : owned) spmv::dev_free(q);
     }
 };

@@ -337,7 +337,8 @@ __device__ __forceinline__ void ell_long_row(const EllArgs& a, int32_t i, double
 // positions s*C + l*R .. + R-1, reading R values and R indices per slot with
 // vector loads (R = 2: 16 + 8 bytes, R = 4: 2 x 16 + 16 bytes).  Wide slices
 // are split into chunks of `unit_width` slots whose partial sums are added in
-// chunk order by the last chunk to finish.  y is written through perm.
+// chunk order by the last chunk to finish.  y is written through perm (ADD:
+// added to, for the second and later column panels of a paneled matrix).
 struct SellArgs {
     const int2* units;
     const int64_t* slice_ptr;
@@ -353,7 +354,7 @@ struct SellArgs {
     double* y;
 };
 
-template <int R>
+template <int R, bool ADD = false>
 __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane) {
     constexpr int C = 32 * R;
     const int2 U = a.units[u];
@@ -398,7 +399,10 @@ __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane
     if (U.y < 0) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (p0 + r < a.m) a.y[a.perm[p0 + r]] = acc[r];
+            if (p0 + r < a.m) {
+                if (ADD) a.y[a.perm[p0 + r]] += acc[r];
+                else a.y[a.perm[p0 + r]] = acc[r];
+            }
         return;
     }
     // chunk of a split slice
@@ -418,7 +422,10 @@ __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane
         double t = 0.0;
 #pragma unroll 8
         for (int32_t c = 0; c < nch; ++c) t += __ldcg(a.partial + (int64_t)(first + c) * C + lane * R + r);
-        if (p0 + r < a.m) a.y[a.perm[p0 + r]] = t;
+        if (p0 + r < a.m) {
+            if (ADD) a.y[a.perm[p0 + r]] += t;
+            else a.y[a.perm[p0 + r]] = t;
+        }
     }
     __syncwarp();
     if (lane == 0) a.counters[first] = 0u;

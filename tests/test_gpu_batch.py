@@ -66,3 +66,12 @@ def test_batch_new_vectors(sp):
         for j, a in enumerate(mats):
             ok, msg = within_bound(a, xs[j].cpu().numpy(), ys[j].cpu().numpy())
             assert ok, (seed, j, msg)
+
+
+def test_batch_refuses_sell_in_column_panels(sp):
+    a = _mats(1)[0]
+    h = sp.spmv_convert(3, sp.DeviceCSR.from_host(a), {"sell_panel_cols": 50})
+    assert h.info()["aux"][3] > 1
+    with pytest.raises(sp.SpmvError) as ei:
+        sp.Batch([h])
+    assert ei.value.name == "INVALID_ARG"

@@ -34,7 +34,8 @@ PARAMS = {
     0: [None, {"csr_block_nnz": 352}],
     1: [None, {"csr5_sigma": 1}, {"csr5_sigma": 4}, {"csr5_sigma": 32}],
     2: [None],
-    3: [None, {"sell_C": 64, "sell_sigma": 1}, {"sell_C": 128, "sell_sigma": -1}, {"sell_C": 32, "sell_sigma": 256}],
+    3: [None, {"sell_C": 64, "sell_sigma": 1}, {"sell_C": 128, "sell_sigma": -1}, {"sell_C": 32, "sell_sigma": 256},
+        {"sell_panel_cols": 700}, {"sell_C": 64, "sell_panel_cols": 1023}],
     4: [None, {"hyb_k": 1}, {"hyb_k": -1}],
 }
 
@@ -99,6 +100,40 @@ def test_unsorted_columns_and_duplicates():
             assert np.array_equal(bits(y), bits(ref)), (fmt, p)
             pt, it, vt = (t.cpu().numpy() for t in sp.spmv_to_csr(h))
             assert np.array_equal(it, idx) and np.array_equal(vt, val)
+
+
+def test_sell_panels_unsorted_columns_and_duplicates():
+    """Column panels of one or a few columns: the product adds the panels in
+    order and the way back restores every entry to its CSR position."""
+    ptr = np.array([0, 4, 4, 7, 9], np.int32)
+    idx = np.array([3, 1, 3, 0, 2, 2, 1, 0, 3], np.int32)
+    val = np.array([1.5, -2.0, 4.0, 8.0, 1.0, 3.0, -1.0, -0.0, 0.0])
+    a = synth.CSR(4, 4, ptr, idx, val, "dups")
+    x = np.array([1.0, 2.0, 3.0, 4.0])
+    ref = oracle.csr_spmv(a, x)
+    for pc in (1, 2, 3):
+        h, y = _run(a, 3, {"sell_panel_cols": pc}, x)
+        info = h.info()
+        assert info["aux"][3] == -(-4 // pc) and info["params"]["sell_panel_cols"] == pc
+        assert np.array_equal(bits(y), bits(ref)), pc
+        pt, it, vt = (t.cpu().numpy() for t in sp.spmv_to_csr(h))
+        assert np.array_equal(pt, ptr) and np.array_equal(it, idx) and np.array_equal(bits(vt), bits(val)), pc
+
+
+def test_sell_panel_rule_splits_large_x():
+    """x of 13e6 doubles (99 MiB, above 96 MiB) is split into panels of at most
+    64 MiB of x; a smaller x stays in one panel."""
+    lens = np.full(3000, 5, np.int32)
+    a = synth.from_lengths_random_cols(lens, 13_000_000, 17, "wide")
+    x = synth.vector(a.n, 18)
+    h, y = _run(a, 3, None, x)
+    info = h.info()
+    assert info["aux"][3] == 2 and info["params"]["sell_panel_cols"] == 6_500_000
+    ok, msg = within_bound(a, x, y)
+    assert ok, msg
+    h1, y1 = _run(a, 3, {"sell_panel_cols": -1}, x)
+    assert h1.info()["aux"][3] == 0 and h1.info()["params"]["sell_panel_cols"] == a.n
+    assert within_bound(a, x, y1)[0]
 
 
 def test_padding_never_multiplied():
