@@ -56,3 +56,40 @@ def test_host_side_argument_errors(lib):
     assert lib.spmv_run(None, None, None, None) == -1
     assert lib.spmv_select(None, None, None, None) == -5
     assert lib.spmv_batch_build(None, 0, None, None) == -1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof and every field offset of the header's structs, compiled by the
+    host C compiler, equal the ctypes structures the binding passes."""
+    import shutil
+    import subprocess
+
+    from paper_1805_11938_gb300 import _abi
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    cuda_inc = None
+    for d in (os.environ.get("CUDA_HOME"), "/usr/local/cuda"):
+        if d and os.path.exists(os.path.join(d, "include", "cuda_runtime_api.h")):
+            cuda_inc = os.path.join(d, "include")
+    if cuda_inc is None:
+        pytest.skip("CUDA headers not found")
+    structs = {"spmv_csr": _abi.spmv_csr, "spmv_params": _abi.spmv_params, "spmv_info": _abi.spmv_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "spmv.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(src), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[f"{name} size"]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
