@@ -316,6 +316,10 @@ def run_batch(args, rank: int, world: int) -> None:
     tb = statistics.mean(t_b)
     ts = statistics.mean(t_s)
     total_b, value = reduce_over_ranks(sum(t_b), 2.0 * total_nnz * args.steps, dist, "cuda")
+    # kernels per replay: the plain task kinds, the CSR tiles (CSR matrices and HYB tails), the HYB tails
+    has_tail = any(i["fmt"] == 4 and i["aux"][1] > 0 for i in infos)
+    launches_per_replay = (int(any(i["fmt"] != 0 or i["nnz"] == 0 for i in infos))
+                           + int(any(i["fmt"] == 0 and i["nnz"] > 0 for i in infos)) + int(has_tail))
     ab = sum(algorithmic_bytes(i["fmt"], i) for i in infos)
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -336,7 +340,7 @@ def run_batch(args, rank: int, world: int) -> None:
                          "alg_bytes_per_launch": ab},
             "batched_ms": tb, "separate_ms": ts, "batched_speedup_over_separate": ts / tb,
             "separate_gflops": 2.0 * total_nnz / ts / 1e6, "bitwise_equal_to_separate": same,
-            "gpu_launches": args.steps * 2, "clocks": clocks}
+            "gpu_launches": args.steps * launches_per_replay, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
 
@@ -465,6 +469,11 @@ def main():
         select_step = lambda: sp.spmv_features(d, feat)  # noqa: E731
         selector_kind = "exhaustive (no trained model found; the step runs the features kernel)"
     sel_ms = statistics.mean(timed(select_step, args.format_steps, 5))
+
+    # ---- gather ceiling of this matrix's index stream: val[k] * x[idx[k]] for
+    # every entry, one gather and one DFMA each, no row structure
+    probe_part = torch.empty(sp._abi.PROBE_PARTIALS, dtype=torch.float64, device="cuda")
+    probe_ms = statistics.mean(timed(lambda: sp.spmv_probe_gather(d, x, probe_part), args.format_steps, 5))
     hc = handles[chosen]
 
     def step():
@@ -578,7 +587,12 @@ def main():
                    "l2": "flushed: 256 MiB written before every timed step", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": f"{FORMATS[chosen]} product", "kernel_ms": kms,
-                     "alg_bytes_per_launch": ab, "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy, burst)"},
+                     "alg_bytes_per_launch": ab, "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy, burst)",
+                     "gather_ceiling": {"ms": probe_ms, "g_gathers_per_s": a.nnz / probe_ms / 1e6,
+                                        "frac": probe_ms / kms,
+                                        "what": "spmv_probe_gather on this matrix's idx/val: one random gather and "
+                                                "one DFMA per entry, no row structure, L2 flushed; frac = its time / "
+                                                "the product's"}},
         "e2e": {"value": 2.0 * a.nnz / e2e_ms / 1e6, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * a.n,
                 "d2h_bytes_per_step": 8 * a.m, "ms_per_step": e2e_ms, "steps": n_e2e,
                 "copies": "pinned host x in and y out every step, double-buffered on two copy streams "

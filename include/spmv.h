@@ -255,6 +255,23 @@ SPMV_API void spmv_batch_free(spmv_batch* b);
  *  - Asynchronous on `stream`; two kernel launches. */
 SPMV_API int spmv_csr_run_noalloc(const spmv_csr* csr, const double* x, double* y, cudaStream_t stream);
 
+/* ------------------------------------------------------------ measurement */
+
+/* The gather ceiling of a product on a given index stream: sums
+ * val[k] * x[idx[k]] over k < nnz with one random gather and one DFMA per
+ * entry and no row structure (a grid-stride stream over the arrays with
+ * coalesced loads of idx and val and the gathers through the read-only path,
+ * as the product kernels issue them).  Not in the paper: a measurement aid;
+ * its time on a matrix's own idx/val is the practical roofline of an SpMV on
+ * that matrix when the gathers, not HBM, bound it.
+ *  - idx, val: nnz entries, x: indexed by idx; all device memory.
+ *  - partial: SPMV_PROBE_PARTIALS doubles of device memory, overwritten with
+ *    one partial sum per thread (their sum is the total).
+ *  - Asynchronous on `stream`; one launch. */
+#define SPMV_PROBE_PARTIALS (152 * 8 * 256)
+SPMV_API int spmv_probe_gather(const int32_t* idx, const double* val, int64_t nnz, const double* x, double* partial,
+                               cudaStream_t stream);
+
 /* --------------------------------------------------------- fault testing */
 
 /* Make the k-th device allocation from now fail with SPMV_ERR_ALLOC

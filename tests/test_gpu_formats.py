@@ -311,3 +311,14 @@ def test_full_size_ell_refused_under_cap(cfg2):
     with pytest.raises(sp.SpmvError) as ei:
         sp.spmv_convert(sp.SPMV_ELL, d, {"max_bytes": 8 << 30})
     assert ei.value.name == "TOO_LARGE"
+
+
+def test_gather_probe_sums_every_product():
+    """The gather-ceiling probe touches every entry once: with integer values
+    its partial sums add up exactly to sum(val[k] * x[idx[k]])."""
+    for mi in (1, 9, 10):
+        a = synth.with_integer_values(MATS[mi], 31 + mi)
+        x = synth.integers(a.n, 32 + mi, -16, 16)
+        part = sp.spmv_probe_gather(sp.DeviceCSR.from_host(a), torch.as_tensor(x).cuda()).cpu().numpy()
+        exact = int(np.sum(a.val.astype(np.int64) * x.astype(np.int64)[a.idx]))
+        assert part.sum() == float(exact), (a.name, part.sum(), exact)
