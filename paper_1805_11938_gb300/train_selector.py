@@ -11,6 +11,10 @@ full-batch Adam training loop (spmv_mlp_train) and inference
 (spmv_mlp_forward) all run in this library's CUDA kernels.  The split is 800
 training / 200 held-out matrices by a seeded shuffle.
 
+Steps and learning rate are chosen by five-fold cross-validation on the 800
+training matrices (the paper trains with five-fold cross-validation); the
+held-out 200 play no part in the choice.
+
 Two models come from one profiling table: --key ms learns the fastest format
 for one product of a matrix alone (spmv_select's model), --key ms_batch the
 format with the best throughput when the GPU is kept busy, as in a batch
@@ -140,6 +144,28 @@ def summary(records: list, idx, pred, key: str = "ms") -> dict:
     return out
 
 
+SETTINGS = tuple({"steps": st, "lr": lr} for st in (1500, 3000, 6000) for lr in (1e-3, 3e-3, 1e-2))
+
+
+def cross_validate(records: list, train_idx, key: str = "ms", folds: int = 5, settings=SETTINGS, seed: int = 1):
+    """Five-fold cross-validation on the training matrices only (Sec. V-B):
+    for each setting, the mean over the folds of the held-in-fold % of best;
+    returns (best setting, table).  Ties go to the earlier setting."""
+    train_idx = np.asarray(train_idx)
+    parts = np.array_split(train_idx, folds)
+    table = []
+    for st in settings:
+        scores = []
+        for f in range(folds):
+            val = parts[f]
+            fit_idx = np.concatenate([parts[g] for g in range(folds) if g != f])
+            model = fit(records, fit_idx, st["steps"], st["lr"], seed, key)
+            scores.append(float(pct_of_best(records, val, predict(model, records, val), key).mean()))
+        table.append({**st, "cv_mean_pct_of_best": 100 * float(np.mean(scores))})
+    best = max(range(len(table)), key=lambda i: (table[i]["cv_mean_pct_of_best"], -i))
+    return settings[best], table
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--table", required=True)
@@ -148,16 +174,22 @@ def main():
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--key", default="ms", choices=sorted(LABEL_OF))
+    ap.add_argument("--no-cv", action="store_true", help="train with --steps/--lr instead of choosing them by CV")
     args = ap.parse_args()
     recs = load_table(args.table)
     assert [r["index"] for r in recs] == list(range(len(recs))), "table must hold matrices 0..n-1"
     tr, te = split(len(recs), n_train=int(round(0.8 * len(recs))))
+    cv = None
+    if not args.no_cv:
+        chosen, table = cross_validate(recs, tr, args.key, seed=args.seed)
+        args.steps, args.lr = chosen["steps"], chosen["lr"]
+        cv = {"folds": 5, "chosen": chosen, "table": table}
     model = fit(recs, tr, args.steps, args.lr, args.seed, args.key)
     ev_train = summary(recs, tr, predict(model, recs, tr), args.key)
     ev_test = summary(recs, te, predict(model, recs, te), args.key)
     out = {"params": model["params"].tolist(), "lo": model["lo"].tolist(), "hi": model["hi"].tolist(),
            "features": "spmv_features v1 (16 features, rows sampled above 16384)",
-           "timing": args.key,
+           "timing": args.key, "cross_validation": cv,
            "training": {k: model[k] for k in ("steps", "lr", "seed", "loss_first", "loss_last")},
            "n_train": len(tr), "n_test": len(te), "train": ev_train, "held_out": ev_test}
     with open(args.out, "w") as f:
