@@ -5,7 +5,7 @@ profiling -- n_rows, n_cols, nnz_frac, nnz_min, nnz_max, nnz_avg, nnz_std and
 "variation".  Eight more are added for the GPU formats.  Definitions (the paper
 gives names only; the readings are ours):
 
-Row sample R: all rows if M <= 16384, else rows floor(k*M/16384), k < 16384.
+Row sample R: all rows if M <= 8192, else rows floor(k*M/8192), k < 8192.
 len_i = ptr[i+1] - ptr[i];  L = sum over R of len_i;  |R| = count.
 
  0 n_rows      M
@@ -40,7 +40,7 @@ import numpy as np
 FEATURE_NAMES = ("n_rows", "n_cols", "nnz_frac", "nnz_min", "nnz_max", "nnz_avg", "nnz_std", "variation",
                  "log2_nnz", "ell_fill", "hyb_tail", "diag_spread", "bandwidth", "empty_frac", "long_frac",
                  "sell32_fill")
-SAMPLE_ROWS = 16384
+SAMPLE_ROWS = 8192
 LEN_CAP = 512
 SPREAD_ENTRIES = 16
 LONG_ROW = 32

@@ -3,8 +3,8 @@
 // representation label out; here a 16-64-64-5 multilayer perceptron, one of
 // the alternatives of Sec. V-D), with its training kernels.
 //
-// Feature definitions (rows sampled when M > 16384):
-//   R = all rows, or rows floor(k*M/16384) for k < 16384; len_i = ptr[i+1]-ptr[i]
+// Feature definitions (rows sampled when M > 8192):
+//   R = all rows, or rows floor(k*M/8192) for k < 8192; len_i = ptr[i+1]-ptr[i]
 //   0 n_rows  1 n_cols  2 nnz/(M*N)  3 min len  4 max len  5 nnz/M
 //   6 std of len over R  7 std/mean  8 log2(max(nnz,1))  9 mean/max
 //  10 HYB tail fraction with K from R (lengths capped at 512)
@@ -34,7 +34,7 @@ namespace spmv {
 
 constexpr int kFeatCtas = 8;
 constexpr int kFeatThreads = 1024;
-constexpr int kSample = 16384;
+constexpr int kSample = 8192;  // = kFeatCtas * kFeatThreads: one sampled row per thread
 constexpr int kLenCap = 512;
 constexpr int kSpread = 16;
 
@@ -123,35 +123,36 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
     for (int b = tid; b <= kLenCap; b += kFeatThreads) hist[b] = 0;
     __syncthreads();
 
-    // ---- phase 1: every CTA reduces its share of the sampled rows.  A thread
-    // holds at most two sampled rows (8 CTAs x 1024 threads, 16384 samples);
-    // both rows' loads are issued together.  Row of sample k: k*M/S, with
-    // S = 16384 = 2^14 whenever M > S (a shift), else k.
+    // ---- phase 1: every CTA reduces its share of the sampled rows, one per
+    // thread (8 CTAs x 1024 threads, 8192 samples).  Row of sample k: k*M/S,
+    // with S = 8192 = 2^13 whenever M > S (a shift), else k.
     const int64_t S = m < kSample ? m : kSample;
     unsigned long long sl = 0, sq = 0, ssum = 0, scnt = 0;
     int mn = 0x7fffffff, mx = 0, band = 0;
     unsigned emp = 0, lng = 0;
     {
-        const int64_t kk[2] = {(int64_t)rank * kFeatThreads + tid, (int64_t)rank * kFeatThreads + tid + kFeatCtas * kFeatThreads};
-        int64_t ii[2];
-        int32_t p0[2], p1[2];
+        constexpr int kRows = kSample / (kFeatCtas * kFeatThreads);  // sampled rows per thread
+        static_assert(kSample == kFeatCtas * kFeatThreads * kRows && kSample == 1 << 13, "sample layout");
+        int64_t kk[kRows], ii[kRows];
+        int32_t p0[kRows], p1[kRows];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            ii[r] = m > kSample ? ((kk[r] * (int64_t)m) >> 14) : kk[r];
+        for (int r = 0; r < kRows; ++r) {
+            kk[r] = (int64_t)rank * kFeatThreads + tid + (int64_t)r * kFeatCtas * kFeatThreads;
+            ii[r] = m > kSample ? ((kk[r] * (int64_t)m) >> 13) : kk[r];
             const bool on = kk[r] < S;
             p0[r] = on ? ptr[ii[r]] : 0;
             p1[r] = on ? ptr[ii[r] + 1] : 0;
         }
-        int32_t c[2][kSpread];
+        int32_t c[kRows][kSpread];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < kRows; ++r) {
             const int32_t len = p1[r] - p0[r];
             const int ne = len < kSpread ? len : kSpread;
 #pragma unroll
             for (int q = 0; q < kSpread; ++q) c[r][q] = q < ne ? __ldg(idx + p0[r] + q) : (int32_t)ii[r];
         }
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < kRows; ++r) {
             const bool on = kk[r] < S;
             const int32_t len = p1[r] - p0[r];
             if (on) {

@@ -27,8 +27,8 @@ def _feature_cases():
     lens = np.array([0, 0, 700, 0, 3, 0, 0, 70, 1, 0] * 50, np.int32)
     return [
         synth.config1(),
-        synth.powerlaw(20_000, 3, xmax=3000, lmax=3000),  # sampled rows (M > 16384)
-        synth.powerlaw(16_384, 4),                        # exactly the sample size
+        synth.powerlaw(20_000, 3, xmax=3000, lmax=3000),  # sampled rows (M > 8192)
+        synth.powerlaw(8_192, 4),                         # exactly the sample size
         synth.banded(100_000, 40, 5),
         synth.stencil(synth.STENCIL_7PT_3D, 30, 30, 30, 6),
         synth.blockdiag(777, 64, 7),

@@ -382,16 +382,16 @@ def test_features_laplacian_64():
 
 
 def test_features_sampled_rows():
-    """Above 16384 rows only rows floor(k*M/16384) count: make exactly those long."""
+    """Above 8192 rows only rows floor(k*M/8192) count: make exactly those long."""
     m = 40_000
-    sampled = set((k * m) // 16384 for k in range(16384))
+    sampled = set((k * m) // 8192 for k in range(8192))
     lens = np.array([40 if i in sampled else 0 for i in range(m)], np.int32)
     ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
     idx = np.concatenate([np.arange(40) for _ in sampled]).astype(np.int32)
     a = synth.CSR(m, 40, ptr, idx, np.ones(int(ptr[-1])))
     f = oracle.features(a)
     assert f[3] == 40 and f[4] == 40 and f[6] == 0 and f[13] == 0 and f[14] == 1.0  # sample sees only long rows
-    assert f[5] == 40 * 16384 / m  # nnz_avg is exact, not sampled
+    assert f[5] == 40 * 8192 / m  # nnz_avg is exact, not sampled
     assert f[10] == 0.0 and f[9] == 1.0
 
 
