@@ -111,8 +111,12 @@ typedef struct {
     int64_t device_bytes;   /* memory owned by the handle */
     int64_t stored_slots;   /* value slots stored, padding included */
     spmv_params params;     /* resolved tuning parameters (hyb_k: the K used) */
-    int64_t aux[4];         /* format detail: CSR units, CSR5 tiles, ELL K, SELL slices,
-                               HYB tail entries; see spmv_handle_array for the arrays */
+    int64_t aux[4];         /* format detail (see spmv_handle_array for the arrays):
+                               CSR  {warp tiles, 0, 0, 0}
+                               CSR5 {tiles, tiles listing their rows, empty rows, 0}
+                               ELL  {K, rows left to whole blocks, their length threshold, 0}
+                               SELL {slices, warp units, longest row, column panels (0: one)}
+                               HYB  {COO tail entries, tail rows, K, tail warp tiles} */
 } spmv_info;
 
 /* ---------------------------------------------------------------- basics */
@@ -137,9 +141,10 @@ SPMV_API int spmv_convert(spmv_fmt fmt, const spmv_csr* csr, const spmv_params* 
 
 /* y = A x (Sec. II-A), y overwritten (beta = 0).  x holds N doubles and y M
  * doubles, both device memory.  Asynchronous on `stream`; no host sync.
- * Launches the format's kernels (one or two launches).  Runs of one handle
- * must not overlap on the GPU (they share the handle's small scratch for
- * rows split across warps); runs of different handles may. */
+ * Launches the format's kernels: one (CSR, CSR5, ELL, SELL), two (HYB with a
+ * COO tail), or one per column panel (SELL in panels, in panel order).  Runs of one handle must not overlap on the GPU
+ * (they share the handle's small scratch for rows split across warps); runs
+ * of different handles may. */
 SPMV_API int spmv_run(const spmv_handle* h, const double* x, double* y, cudaStream_t stream);
 
 /* Write A back as CSR (ptr[M+1], idx[nnz], val[nnz], device, caller-owned).
