@@ -323,9 +323,11 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
 }
 
 // Warp w takes units w, w + warps, ... (the sort puts the widest slices,
-// split into chunks, first, so the static split is balanced).
+// split into chunks, first, so the static split is balanced).  Register
+// budgets keep 8 / 5 / 4 blocks resident for C = 32 / 64 / 128 (measured:
+// C = 32 on the power-law matrix 77.6 us at 40 registers, 74.8 at 32).
 template <int R, bool ADD>
-__global__ void __launch_bounds__(256) k_sell(dev::SellArgs a, int32_t nu) {
+__global__ void __launch_bounds__(256, R == 1 ? 8 : (R == 2 ? 5 : 4)) k_sell(dev::SellArgs a, int32_t nu) {
     const int32_t stride = (int32_t)gridDim.x * 8;
     for (int32_t u = (int32_t)(blockIdx.x * 8 + (threadIdx.x >> 5)); u < nu; u += stride)
         dev::sell_unit<R, ADD>(a, u, threadIdx.x & 31);
