@@ -1,5 +1,5 @@
 // Shared host helpers and small device utilities: errors, allocation, CSR
-// validation, exclusive scan, row lengths and CSR row-block units.
+// validation, exclusive scan, row lengths and the CSR nonzero tiles.
 #include <atomic>
 #include <cstring>
 #include <mutex>
