@@ -76,3 +76,20 @@ def test_random_matrices_every_format(sp, seed):
             pt, it, vt = (t.cpu().numpy() for t in sp.spmv_to_csr(h))
             assert np.array_equal(pt, a.ptr) and np.array_equal(it, a.idx) and np.array_equal(bits(vt), bits(a.val)), \
                 (a.name, sp.FORMATS[fmt], p)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_matrices_features(sp, seed):
+    """The 16 features of random matrices around the sampling boundary (8192
+    rows), with empty rows and rows past the 512 length cap, against the oracle."""
+    rng = np.random.default_rng(5000 + seed)
+    m = int(rng.choice([1, 7, 8191, 8192, 8193, 20_000, int(rng.integers(2, 60_000))]))
+    n = int(rng.integers(1, 100_000))
+    lens = np.where(rng.random(m) < 0.2, 0, rng.integers(1, 40, size=m))
+    lens[rng.random(m) < 0.01] = 700
+    ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    a = synth.CSR(m, n, ptr, rng.integers(0, n, size=int(ptr[-1])).astype(np.int32), np.ones(int(ptr[-1])),
+                  f"feat{seed}")
+    f = sp.spmv_features(sp.DeviceCSR.from_host(a)).cpu().numpy()
+    ref = oracle.features(a).astype(np.float32)
+    assert np.allclose(f, ref, rtol=2e-6, atol=0), (a.name, np.stack([f, ref]))
