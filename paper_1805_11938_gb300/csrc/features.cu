@@ -12,10 +12,15 @@
 //  13 fraction of empty rows  14 fraction of rows with len >= 32
 //  15 SELL-32 fill over R sorted, lengths capped at 512
 //
-// The features kernel is one cluster of 8 CTAs x 1024 threads: each CTA
-// reduces its share of the sampled rows, then CTA 0 combines the eight
-// partial results through distributed shared memory (no global scratch, no
-// atomics across CTAs) and, for selection, runs the network.
+// The features kernel is one thread-block cluster (16 CTAs x 512 threads where
+// the device can place one, else 8 x 1024), one sampled row per thread.  Each
+// CTA reduces its rows, then adds its statistics and its length histogram
+// into CTA 0's shared memory with cluster shared-memory atomics (no global
+// scratch); after one cluster barrier two warps of CTA 0 finish: warp 1 scans
+// the histogram while warp 0 evaluates the features as straight-line code,
+// then, for a selection, both run the network.  A lone warp's dependent
+// instructions are the cost there, so that code avoids divergent per-feature
+// branches and keeps its divisions independent.
 #include <cooperative_groups.h>
 #include <cuda_pipeline.h>
 
@@ -32,254 +37,296 @@ struct spmv_model {
 
 namespace spmv {
 
-constexpr int kFeatCtas = 8;
-constexpr int kFeatThreads = 1024;
-constexpr int kSample = 8192;  // = kFeatCtas * kFeatThreads: one sampled row per thread
+constexpr int kFeatCtasSmall = 8;   // CTAs of the features cluster: the portable size
+constexpr int kFeatCtasLarge = 16;  // and the largest, where the device allows it
+constexpr int kSample = 8192;       // sampled rows: one per thread of the cluster
 constexpr int kLenCap = 512;
 constexpr int kSpread = 16;
 
 // parameter offsets inside the flat vector
 constexpr int oW1 = 0, oB1 = 1024, oW2 = 1088, oB2 = 5184, oW3 = 5248, oB3 = 5568, kNP = 5573;
 
-struct FeatStats {  // one CTA's partial statistics of the sampled rows
-    unsigned long long sum_len, sum_sq, spread_sum, spread_cnt;
-    int min_len, max_len, band;
-    unsigned empty, longc;
-};
-
 // Transform and min-max scaling of one feature.  FP32 on purpose: this GPU's
 // FP64 pipe makes double log2/division/sqrt several microseconds slower, and
-// the features are float32 values to begin with.
+// the features are float32 values to begin with.  Both logarithms are taken
+// and one is selected, so lanes scaling different features do not diverge.
+// Quotients here and in the features use the two-ulp division (reciprocal and
+// multiply, no branch to a slow path), so independent ones overlap; every
+// operand lies far inside its range.
 __device__ __forceinline__ float feat_transform(int j, float f) {
-    if (j == 0 || j == 1 || j == 3 || j == 4 || j == 5 || j == 6 || j == 11 || j == 12) return log2f(1.0f + f);
-    if (j == 2) return -log2f(fmaxf(f, 0x1.0p-60f));
-    return f;
+    constexpr unsigned kLog1p = (1u << 0) | (1u << 1) | (1u << 3) | (1u << 4) | (1u << 5) | (1u << 6) | (1u << 11) |
+                                (1u << 12);
+    const float a = log2f(1.0f + f);
+    const float b = -log2f(fmaxf(f, 0x1.0p-60f));
+    return ((kLog1p >> j) & 1u) ? a : (j == 2 ? b : f);
 }
 
 __device__ __forceinline__ float feat_scale(int j, float f, const float* lo, const float* hi) {
     const float t = feat_transform(j, f);
     const float span = hi[j] - lo[j];
-    if (!(span > 0.0f)) return 0.0f;
-    const float x = (t - lo[j]) / span;
-    return x < 0.0f ? 0.0f : (x > 1.0f ? 1.0f : x);
+    const float x = __fdividef(t - lo[j], span);
+    return !(span > 0.0f) ? 0.0f : (x < 0.0f ? 0.0f : (x > 1.0f ? 1.0f : x));
 }
 
 // Barrier of the first two warps only (named barrier 1), for the tail of the
 // features kernel that runs in warps 0 and 1 after the others have left.
 __device__ __forceinline__ void tail_sync() { asm volatile("bar.sync 1, 64;" ::: "memory"); }
 
-// 16 -> 64 -> 64 -> 5 forward for one sample in threads 0..63 (warps 0 and 1);
-// th in shared memory.  Thread j computes hidden unit j of each layer as one
-// dot product (consecutive j: conflict-free weight reads, broadcast inputs).
-__device__ void mlp_forward_64(const float* th, const float* xs, float* h1, float* h2, float* z) {
-    const int j = threadIdx.x;
-    float a = th[oB1 + j];
+// The cluster barrier in its two halves: arrive releases this thread's earlier
+// shared-memory writes to the cluster, wait acquires everyone's.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) a = fmaf(xs[i], th[oW1 + i * 64 + j], a);
-    h1[j] = a > 0.f ? a : 0.f;
-    tail_sync();
-    a = th[oB2 + j];
-#pragma unroll 16
-    for (int i = 0; i < 64; ++i) a = fmaf(h1[i], th[oW2 + i * 64 + j], a);
-    h2[j] = a > 0.f ? a : 0.f;
-    tail_sync();
-    if (j < 5) {
-        a = th[oB3 + j];
-#pragma unroll 16
-        for (int i = 0; i < 64; ++i) a = fmaf(h2[i], th[oW3 + i * 5 + j], a);
-        z[j] = a;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(dev::kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ unsigned warp_sum_u32(unsigned v) { return __reduce_add_sync(dev::kFull, v); }
+__device__ __forceinline__ int warp_min_i32(int v) { return __reduce_min_sync(dev::kFull, v); }
+__device__ __forceinline__ int warp_max_i32(int v) { return __reduce_max_sync(dev::kFull, v); }
+__device__ __forceinline__ float u64_to_f32(unsigned long long v) { return (float)v; }
+
+// 16 -> 64 -> 64 -> 5 forward for one sample in threads 0..63 (warps 0 and
+// 1), th in shared memory, xs the 16 scaled features.  Hidden unit j of each
+// layer is thread j's dot product, split over independent accumulators so the
+// FMA chains stay short (consecutive j: conflict-free weight reads; the inputs
+// are broadcast).  Warp 0 alone computes the five outputs, four lanes each
+// (output c in lanes 4c..4c+3), writes them to z_out if given, and returns in
+// every lane the index of the largest (the first of equal maxima).  Warp 1
+// returns -1 once the second layer is done.
+__device__ int mlp_forward_64(const float* th, const float* xs, float* h1, float* h2, float* z_out) {
+    const int j = threadIdx.x;
+    float a0 = th[oB1 + j], a1 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 16; i += 2) {
+        a0 = fmaf(xs[i], th[oW1 + i * 64 + j], a0);
+        a1 = fmaf(xs[i + 1], th[oW1 + (i + 1) * 64 + j], a1);
     }
+    a0 += a1;
+    h1[j] = a0 > 0.f ? a0 : 0.f;
     tail_sync();
+    float c0 = th[oB2 + j], c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    const float4* h14 = reinterpret_cast<const float4*>(h1);
+#pragma unroll
+    for (int i = 0; i < 64; i += 4) {
+        const float4 v = h14[i / 4];
+        c0 = fmaf(v.x, th[oW2 + i * 64 + j], c0);
+        c1 = fmaf(v.y, th[oW2 + (i + 1) * 64 + j], c1);
+        c2 = fmaf(v.z, th[oW2 + (i + 2) * 64 + j], c2);
+        c3 = fmaf(v.w, th[oW2 + (i + 3) * 64 + j], c3);
+    }
+    c0 = (c0 + c1) + (c2 + c3);
+    h2[j] = c0 > 0.f ? c0 : 0.f;
+    tail_sync();
+    if (j >= 32) return -1;
+    // lane 4c + p sums inputs p, p + 4, ..., p + 60 of output c (conflict-free reads)
+    const int c = j >> 2, part = j & 3, cc = c < 5 ? c : 0;
+    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+    for (int t = 0; t < 16; t += 2) {
+        d0 = fmaf(h2[part + 4 * t], th[oW3 + (part + 4 * t) * 5 + cc], d0);
+        d1 = fmaf(h2[part + 4 * (t + 1)], th[oW3 + (part + 4 * (t + 1)) * 5 + cc], d1);
+    }
+    float zc = d0 + d1;
+    zc += __shfl_xor_sync(dev::kFull, zc, 1);
+    zc += __shfl_xor_sync(dev::kFull, zc, 2);
+    zc += th[oB3 + cc];
+    if (z_out && part == 0 && c < 5) z_out[c] = zc;
+    float best = __shfl_sync(dev::kFull, zc, 0);
+    int bi = 0;
+#pragma unroll
+    for (int q = 1; q < 5; ++q) {
+        const float v = __shfl_sync(dev::kFull, zc, 4 * q);
+        if (v > best) {
+            best = v;
+            bi = q;
+        }
+    }
+    return bi;
 }
 
-__global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads)
-    k_features(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t m, int32_t n,
+// The features kernel: one cluster of CTAS CTAs, kSample / CTAS threads each,
+// one sampled row per thread.  VEC: idx is 16-byte aligned and each sampled
+// row's first entries are read as the aligned 16-byte words covering them
+// (at most five), else one 4-byte load each (at most sixteen).
+template <int CTAS, bool VEC>
+__global__ void __launch_bounds__(kSample / CTAS)
+    k_features(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t m, int32_t n, int64_t nnz,
                float* __restrict__ feat_out, const float* __restrict__ model_params, const float* __restrict__ lo,
                const float* __restrict__ hi, int32_t* __restrict__ fmt_out, float* __restrict__ logits_out) {
+    constexpr int T = kSample / CTAS;
+    constexpr int NW = T / 32;
+    static_assert(kSample == 1 << 13 && T * CTAS == kSample && NW <= 32 && T >= 64, "sample layout");
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank();
-    __shared__ unsigned hist[kLenCap + 1];                // this CTA's length histogram
-    __shared__ FeatStats parts[kFeatCtas];                // in CTA 0: every CTA's statistics
-    __shared__ unsigned hists[kFeatCtas * (kLenCap + 1)]; // in CTA 0: every CTA's histogram
-    __shared__ unsigned long long red_u[32][4];
-    __shared__ int red_i[32][3];
-    __shared__ unsigned red_c[32][2];
+    // In CTA 0 these end as the cluster's totals: the length histogram (lengths
+    // capped at 512), sum of len, of len^2 and of |col - row| over the first 16
+    // entries; min and max len, max |col - row|; empty rows, rows with
+    // len >= 32, entries in the spread sums.
+    __shared__ unsigned hist[kLenCap + 1];
+    __shared__ unsigned long long tot_u[3];
+    __shared__ int tot_i[3];
+    __shared__ unsigned tot_c[3];
+    __shared__ unsigned long long red_u[NW][3];
+    __shared__ unsigned red_c[NW][6];
+    __shared__ float qop[4];
+    __shared__ __align__(16) float wsm[kNP + 3 + 32];
+    __shared__ int32_t nnz_sm;
+    __shared__ __align__(16) float xs[16], h1[64], h2[64];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // CTA 0 starts copying what its tail needs into shared memory now
     // (asynchronous copies, waited for just before the tail): nnz = ptr[m]
     // and, for a selection, the network and the scaling table.
-    __shared__ __align__(16) float wsm[kNP + 3 + 32];
-    __shared__ int32_t nnz_sm;
     if (rank == 0) {
         if (tid == 0) __pipeline_memcpy_async(&nnz_sm, ptr + m, 4);
         if (model_params) {
-            for (int c = tid; c < kNP / 4; c += kFeatThreads) __pipeline_memcpy_async(wsm + 4 * c, model_params + 4 * c, 16);
+            for (int c = tid; c < kNP / 4; c += T) __pipeline_memcpy_async(wsm + 4 * c, model_params + 4 * c, 16);
             if (tid < kNP % 4) __pipeline_memcpy_async(wsm + (kNP / 4) * 4 + tid, model_params + (kNP / 4) * 4 + tid, 4);
             if (tid < 4) __pipeline_memcpy_async(wsm + kNP + 3 + 4 * tid, lo + 4 * tid, 16);
             else if (tid < 8) __pipeline_memcpy_async(wsm + kNP + 3 + 16 + 4 * (tid - 4), hi + 4 * (tid - 4), 16);
         }
         __pipeline_commit();
     }
-    for (int b = tid; b <= kLenCap; b += kFeatThreads) hist[b] = 0;
+    for (int b = tid; b <= kLenCap; b += T) hist[b] = 0;
+    if (tid < 3) {
+        tot_u[tid] = 0;
+        tot_i[tid] = tid == 0 ? 0x7fffffff : 0;
+        tot_c[tid] = 0;
+    }
     __syncthreads();
+    cluster_arrive();  // waited for before the CTAs add into CTA 0's totals
 
-    // ---- phase 1: every CTA reduces its share of the sampled rows, one per
-    // thread (8 CTAs x 1024 threads, 8192 samples).  Row of sample k: k*M/S,
-    // with S = 8192 = 2^13 whenever M > S (a shift), else k.
+    // ---- phase 1: one sampled row per thread.  Row of sample k: k*M/S, with
+    // S = 8192 = 2^13 whenever M > S (a shift), else k.
     const int64_t S = m < kSample ? m : kSample;
-    unsigned long long sl = 0, sq = 0, ssum = 0, scnt = 0;
-    int mn = 0x7fffffff, mx = 0, band = 0;
-    unsigned emp = 0, lng = 0;
-    {
-        constexpr int kRows = kSample / (kFeatCtas * kFeatThreads);  // sampled rows per thread
-        static_assert(kSample == kFeatCtas * kFeatThreads * kRows && kSample == 1 << 13, "sample layout");
-        int64_t kk[kRows], ii[kRows];
-        int32_t p0[kRows], p1[kRows];
+    const int64_t k = (int64_t)rank * T + tid;
+    const bool on = k < S;
+    const int32_t i = (int32_t)(m > kSample ? ((k * (int64_t)m) >> 13) : k);
+    const int32_t p0 = on ? ptr[i] : 0;
+    const int32_t len = on ? ptr[i + 1] - p0 : 0;
+    const int ne = len < kSpread ? len : kSpread;
+    unsigned long long ssum = 0;
+    int band = 0;
+    if constexpr (VEC) {
+        const int32_t base = p0 & ~3;
+        const int off = p0 - base, nv = (off + ne + 3) >> 2;
+        int32_t w[4 * 5];
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            kk[r] = (int64_t)rank * kFeatThreads + tid + (int64_t)r * kFeatCtas * kFeatThreads;
-            ii[r] = m > kSample ? ((kk[r] * (int64_t)m) >> 13) : kk[r];
-            const bool on = kk[r] < S;
-            p0[r] = on ? ptr[ii[r]] : 0;
-            p1[r] = on ? ptr[ii[r] + 1] : 0;
-        }
-        int32_t c[kRows][kSpread];
+        for (int v = 0; v < 5; ++v) {
+            const int64_t e0 = (int64_t)base + 4 * v;
+            w[4 * v] = w[4 * v + 1] = w[4 * v + 2] = w[4 * v + 3] = i;
+            if (v < nv) {  // the word holds entries of the window
+                if (e0 + 4 <= nnz) {
+                    const int4 t = __ldg(reinterpret_cast<const int4*>(idx + e0));
+                    w[4 * v] = t.x;
+                    w[4 * v + 1] = t.y;
+                    w[4 * v + 2] = t.z;
+                    w[4 * v + 3] = t.w;
+                } else {  // the end of idx: the row's own entries one by one
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const int32_t len = p1[r] - p0[r];
-            const int ne = len < kSpread ? len : kSpread;
-#pragma unroll
-            for (int q = 0; q < kSpread; ++q) c[r][q] = q < ne ? __ldg(idx + p0[r] + q) : (int32_t)ii[r];
-        }
-#pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-            const bool on = kk[r] < S;
-            const int32_t len = p1[r] - p0[r];
-            if (on) {
-                sl += (unsigned long long)len;
-                sq += (unsigned long long)len * (unsigned long long)len;
-                mn = min(mn, len);
-                mx = max(mx, len);
-                emp += len == 0;
-                lng += len >= 32;
-                scnt += (unsigned long long)(len < kSpread ? len : kSpread);
-#pragma unroll
-                for (int q = 0; q < kSpread; ++q) {
-                    const int64_t d = (int64_t)c[r][q] - ii[r];
-                    const int ad = (int)(d < 0 ? -d : d);
-                    ssum += (unsigned long long)ad;
-                    band = max(band, ad);
+                    for (int u = 0; u < 4; ++u)
+                        if (e0 + u < p0 + ne) w[4 * v + u] = __ldg(idx + e0 + u);
                 }
             }
-            // one shared atomic per distinct bin in the warp
-            const unsigned act = __ballot_sync(dev::kFull, on);
-            if (on) {
-                const int bin = len < kLenCap ? len : kLenCap;
-                const unsigned peers = __match_any_sync(act, bin);
-                if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
-            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4 * 5; ++t) {
+            const int d = w[t] - i;
+            const int ad = (t >= off && t < off + ne) ? (d < 0 ? -d : d) : 0;
+            ssum += (unsigned)ad;
+            band = max(band, ad);
+        }
+    } else {
+        int32_t w[kSpread];
+#pragma unroll
+        for (int q = 0; q < kSpread; ++q) w[q] = q < ne ? __ldg(idx + p0 + q) : i;
+#pragma unroll
+        for (int q = 0; q < kSpread; ++q) {
+            const int d = w[q] - i;
+            const int ad = d < 0 ? -d : d;
+            ssum += (unsigned)ad;
+            band = max(band, ad);
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        sl += __shfl_xor_sync(dev::kFull, sl, o);
-        sq += __shfl_xor_sync(dev::kFull, sq, o);
-        ssum += __shfl_xor_sync(dev::kFull, ssum, o);
-        scnt += __shfl_xor_sync(dev::kFull, scnt, o);
-        mn = min(mn, __shfl_xor_sync(dev::kFull, mn, o));
-        mx = max(mx, __shfl_xor_sync(dev::kFull, mx, o));
-        band = max(band, __shfl_xor_sync(dev::kFull, band, o));
-        emp += __shfl_xor_sync(dev::kFull, emp, o);
-        lng += __shfl_xor_sync(dev::kFull, lng, o);
+    {  // one shared atomic per distinct bin in the warp
+        const unsigned act = __ballot_sync(dev::kFull, on);
+        if (on) {
+            const int bin = len < kLenCap ? len : kLenCap;
+            const unsigned peers = __match_any_sync(act, bin);
+            if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
+        }
     }
-    if (lane == 0) {
-        red_u[warp][0] = sl; red_u[warp][1] = sq; red_u[warp][2] = ssum; red_u[warp][3] = scnt;
-        red_i[warp][0] = mn; red_i[warp][1] = mx; red_i[warp][2] = band;
-        red_c[warp][0] = emp; red_c[warp][1] = lng;
+    {
+        const unsigned long long a0 = warp_sum_u64(on ? (unsigned long long)len : 0ull);
+        const unsigned long long a1 = warp_sum_u64(on ? (unsigned long long)len * (unsigned long long)len : 0ull);
+        const unsigned long long a2 = warp_sum_u64(ssum);
+        const int i0 = warp_min_i32(on ? len : 0x7fffffff);
+        const int i1 = warp_max_i32(len);
+        const int i2 = warp_max_i32(band);
+        const unsigned c0 = warp_sum_u32((unsigned)(on && len == 0));
+        const unsigned c1 = warp_sum_u32((unsigned)(len >= 32));
+        const unsigned c2 = warp_sum_u32((unsigned)ne);
+        if (lane == 0) {
+            red_u[warp][0] = a0; red_u[warp][1] = a1; red_u[warp][2] = a2;
+            red_c[warp][0] = (unsigned)i0; red_c[warp][1] = (unsigned)i1; red_c[warp][2] = (unsigned)i2;
+            red_c[warp][3] = c0; red_c[warp][4] = c1; red_c[warp][5] = c2;
+        }
     }
     __syncthreads();
-    // push this CTA's partial into CTA 0's shared memory; one cluster barrier publishes them.
-    // Warp 0 combines the 32 warp partials with shuffles.
-    if (warp == 0) {
-        unsigned long long a0 = red_u[lane][0], a1 = red_u[lane][1], a2 = red_u[lane][2], a3 = red_u[lane][3];
-        int i0 = red_i[lane][0], i1 = red_i[lane][1], i2 = red_i[lane][2];
-        unsigned c0 = red_c[lane][0], c1 = red_c[lane][1];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            a0 += __shfl_xor_sync(dev::kFull, a0, o);
-            a1 += __shfl_xor_sync(dev::kFull, a1, o);
-            a2 += __shfl_xor_sync(dev::kFull, a2, o);
-            a3 += __shfl_xor_sync(dev::kFull, a3, o);
-            i0 = min(i0, __shfl_xor_sync(dev::kFull, i0, o));
-            i1 = max(i1, __shfl_xor_sync(dev::kFull, i1, o));
-            i2 = max(i2, __shfl_xor_sync(dev::kFull, i2, o));
-            c0 += __shfl_xor_sync(dev::kFull, c0, o);
-            c1 += __shfl_xor_sync(dev::kFull, c1, o);
-        }
-        if (lane == 0) {
-            FeatStats p;
-            p.sum_len = a0; p.sum_sq = a1; p.spread_sum = a2; p.spread_cnt = a3;
-            p.min_len = i0; p.max_len = i1; p.band = i2; p.empty = c0; p.longc = c1;
-            *cluster.map_shared_rank(&parts[rank], 0) = p;
+    // Every CTA's totals and histogram have been initialised: add this CTA's
+    // statistics and nonzero histogram bins into CTA 0's (cluster shared-memory
+    // atomics, one statistic per lane); one cluster barrier publishes them.
+    cluster_wait();
+    if (rank != 0) {
+        unsigned* h0 = cluster.map_shared_rank(hist, 0);
+        for (int b = tid; b <= kLenCap; b += T) {
+            const unsigned v = hist[b];
+            if (v) atomicAdd(h0 + b, v);
         }
     }
-    unsigned* h0 = cluster.map_shared_rank(hists, 0);
-    for (int b = tid; b <= kLenCap; b += kFeatThreads) h0[rank * (kLenCap + 1) + b] = hist[b];
+    if (warp == 0) {
+        const bool ok = lane < NW;
+        const unsigned long long a0 = warp_sum_u64(ok ? red_u[lane][0] : 0ull);
+        const unsigned long long a1 = warp_sum_u64(ok ? red_u[lane][1] : 0ull);
+        const unsigned long long a2 = warp_sum_u64(ok ? red_u[lane][2] : 0ull);
+        const int i0 = warp_min_i32(ok ? (int)red_c[lane][0] : 0x7fffffff);
+        const int i1 = warp_max_i32(ok ? (int)red_c[lane][1] : 0);
+        const int i2 = warp_max_i32(ok ? (int)red_c[lane][2] : 0);
+        const unsigned c0 = warp_sum_u32(ok ? red_c[lane][3] : 0u);
+        const unsigned c1 = warp_sum_u32(ok ? red_c[lane][4] : 0u);
+        const unsigned c2 = warp_sum_u32(ok ? red_c[lane][5] : 0u);
+        unsigned long long* tu = cluster.map_shared_rank(tot_u, 0);
+        int* ti = cluster.map_shared_rank(tot_i, 0);
+        unsigned* tc = cluster.map_shared_rank(tot_c, 0);
+        if (lane < 3) atomicAdd(tu + lane, lane == 0 ? a0 : (lane == 1 ? a1 : a2));
+        else if (lane == 3) atomicMin(ti, i0);
+        else if (lane < 6) atomicMax(ti + (lane - 3), lane == 4 ? i1 : i2);
+        else if (lane < 9) atomicAdd(tc + (lane - 6), lane == 6 ? c0 : (lane == 7 ? c1 : c2));
+    }
     cluster.sync();
     if (rank != 0) return;  // CTA 0 holds everything now
-
-    // ---- phase 2 (CTA 0): combine, features, optional selection.  The
-    // histogram ranks are summed by 513 threads; the rest runs in warps 0
-    // and 1 (the scans in warp 0 with shuffles only, lane l owning bins
-    // 17l .. 17l + 16; the network in both warps).
-    __shared__ unsigned hsum[kLenCap + 1];
-    __shared__ FeatStats tot;
-    __shared__ float fs[16], xs[16], h1[64], h2[64], z[5];
-    if (tid <= kLenCap) {
-        unsigned v = 0;
-#pragma unroll
-        for (int r = 0; r < kFeatCtas; ++r) v += hists[r * (kLenCap + 1) + tid];
-        hsum[tid] = v;
-    }
-    if (warp == 0) {  // combine the eight CTA partials (lanes 0..7) with shuffles
-        const int r = lane < kFeatCtas ? lane : 0;
-        const bool on = lane < kFeatCtas;
-        unsigned long long a0 = on ? parts[r].sum_len : 0, a1 = on ? parts[r].sum_sq : 0;
-        unsigned long long a2 = on ? parts[r].spread_sum : 0, a3 = on ? parts[r].spread_cnt : 0;
-        int i0 = on ? parts[r].min_len : 0x7fffffff, i1 = on ? parts[r].max_len : 0, i2 = on ? parts[r].band : 0;
-        unsigned c0 = on ? parts[r].empty : 0, c1 = on ? parts[r].longc : 0;
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-            a0 += __shfl_xor_sync(dev::kFull, a0, o);
-            a1 += __shfl_xor_sync(dev::kFull, a1, o);
-            a2 += __shfl_xor_sync(dev::kFull, a2, o);
-            a3 += __shfl_xor_sync(dev::kFull, a3, o);
-            i0 = min(i0, __shfl_xor_sync(dev::kFull, i0, o));
-            i1 = max(i1, __shfl_xor_sync(dev::kFull, i1, o));
-            i2 = max(i2, __shfl_xor_sync(dev::kFull, i2, o));
-            c0 += __shfl_xor_sync(dev::kFull, c0, o);
-            c1 += __shfl_xor_sync(dev::kFull, c1, o);
-        }
-        if (lane == 0) {
-            tot.sum_len = a0; tot.sum_sq = a1; tot.spread_sum = a2; tot.spread_cnt = a3;
-            tot.min_len = i0; tot.max_len = i1; tot.band = i2; tot.empty = c0; tot.longc = c1;
-        }
-    }
-    __pipeline_wait_prior(0);  // this thread's copies of nnz and the network have landed
-    __syncthreads();
+    __pipeline_wait_prior(0);
+    __syncthreads();  // every thread's copies (nnz, the network, the scaling table) have landed
     if (tid >= 64) return;
+
+    // ---- phase 2 (CTA 0, warps 0 and 1): warp 1 scans the histogram while
+    // warp 0 computes the features that do not need it; then warp 0 finishes
+    // the features and, for a selection, both warps run the network.
     const unsigned cnt = (unsigned)S;
-    unsigned long long upto_k = 0, widths = 0, capped_sum = 0;
-    if (warp == 0) {
-        // c_b = #{len >= b}: suffix sums over the bins (in-lane, then over the lanes)
-        constexpr int PB = 17;  // bins per lane: 32 * 17 = 544 >= 513
-        unsigned c[PB];
+    if (warp == 1) {
+        // c_b = #{len >= b} over the capped histogram: suffix sums, lane l
+        // owning bins 17l .. 17l + 16 (in-lane, then over the lanes).  c_b is
+        // non-increasing, so the bins with c_b >= ceil(S/3) are 1..K of the
+        // HYB rule and the K-dependent sum needs no second pass.
+        constexpr int PB = 17;  // 32 * 17 = 544 >= 513
+        unsigned cb[PB];
         unsigned run = 0;
 #pragma unroll
-        for (int j = PB - 1; j >= 0; --j) {
-            const int bb = lane * PB + j;
-            run += bb <= kLenCap ? hsum[bb] : 0u;
-            c[j] = run;  // in-lane suffix
+        for (int q = PB - 1; q >= 0; --q) {
+            const int bb = lane * PB + q;
+            run += bb <= kLenCap ? hist[bb] : 0u;
+            cb[q] = run;
         }
         unsigned later = run;  // this lane's total, then the totals of later lanes
 #pragma unroll
@@ -289,102 +336,159 @@ __global__ void __cluster_dims__(kFeatCtas, 1, 1) __launch_bounds__(kFeatThreads
         }
         later -= run;
         const unsigned need = (cnt + 2) / 3;
-        unsigned long long k_ok = 0, wpart = 0, cpart = 0;
+        unsigned wpart = 0, cpart = 0, upart = 0;
 #pragma unroll
-        for (int j = 0; j < PB; ++j) {
-            const int bb = lane * PB + j;
-            c[j] += later;
+        for (int q = 0; q < PB; ++q) {
+            const int bb = lane * PB + q;
+            const unsigned v = cb[q] + later;
             if (bb >= 1 && bb <= kLenCap) {
-                k_ok += c[j] >= need;
-                wpart += (c[j] + 31) / 32;
-                cpart += c[j];
+                wpart += (v + 31) >> 5;
+                cpart += v;
+                upart += v >= need ? v : 0u;
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            k_ok += __shfl_xor_sync(dev::kFull, k_ok, o);
-            wpart += __shfl_xor_sync(dev::kFull, wpart, o);
-            cpart += __shfl_xor_sync(dev::kFull, cpart, o);
+        const unsigned widths = warp_sum_u32(wpart);      // SELL-32 slice widths
+        const unsigned capped_sum = warp_sum_u32(cpart);  // sum of min(len, 512)
+        const unsigned upto_k = warp_sum_u32(upart);      // sum of min(len, K)
+        // the operands of the two quotients that need the scans (features 10, 15)
+        const unsigned long long sum_len = tot_u[0];
+        if (lane == 0) {
+            qop[0] = sum_len > 0 ? u64_to_f32(sum_len - upto_k) : 0.0f;
+            qop[1] = sum_len > 0 ? u64_to_f32(sum_len) : 1.0f;
+            qop[2] = widths > 0 ? (float)capped_sum : 1.0f;
+            qop[3] = widths > 0 ? 32.0f * (float)widths : 1.0f;
         }
-        const int K = (int)k_ok;  // c_b is non-increasing, so the bins >= need are 1..K
-        unsigned long long up = 0;
-#pragma unroll
-        for (int j = 0; j < PB; ++j) {
-            const int bb = lane * PB + j;
-            if (bb >= 1 && bb <= K) up += c[j];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) up += __shfl_xor_sync(dev::kFull, up, o);
-        upto_k = up;  // sum min(len, K)
-        widths = wpart;
-        capped_sum = cpart;
     }
-    if (tid < 16) {  // one lane per feature, FP32 (exact integer parts kept in 64 bits)
-        // Every lane evaluates the same straight-line code (no divergent
-        // per-feature paths) and keeps its own feature.
-        const int j = tid;
+    // Warp 0: the features as straight-line code, the same in every lane
+    // (FP32 throughout, exact integer parts in 64 bits), except that each lane
+    // takes the one quotient of its own feature, so the correctly rounded
+    // divisions run side by side rather than one after another.
+    float f = 0.0f;
+    if (warp == 0) {
+        const int j = lane & 15;
+        const unsigned long long sum_len = tot_u[0], sum_sq = tot_u[1], spread_sum = tot_u[2];
+        const int min_len = tot_i[0], max_len = tot_i[1], bandw = tot_i[2];
+        const unsigned empty = tot_c[0], longc = tot_c[1], spread_cnt = tot_c[2];
         const float fc = (float)cnt;
-        const float L = (float)tot.sum_len;
+        const float L = u64_to_f32(sum_len);
         const float mean = L / fc;
-        const float nnz = (float)nnz_sm;
+        const float nz = (float)nnz_sm;
         // std = sqrt(cnt * sum_sq - L^2) / cnt, the difference in exact 128-bit integer arithmetic
-        const unsigned long long a_lo = (unsigned long long)cnt * tot.sum_sq;
-        const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, tot.sum_sq);
-        const unsigned long long b_lo = tot.sum_len * tot.sum_len;
-        const unsigned long long b_hi = __umul64hi(tot.sum_len, tot.sum_len);
+        const unsigned long long a_lo = (unsigned long long)cnt * sum_sq;
+        const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, sum_sq);
+        const unsigned long long b_lo = sum_len * sum_len;
+        const unsigned long long b_hi = __umul64hi(sum_len, sum_len);
         const unsigned long long d_lo = a_lo - b_lo;
         const unsigned long long d_hi = a_hi - b_hi - (a_lo < b_lo ? 1ull : 0ull);
-        const float sd = sqrtf((float)d_hi * 18446744073709551616.0f + (float)d_lo) / fc;
-        // the quotient and the log each lane needs, selected before the one division and log2
+        const float sd = sqrtf(u64_to_f32(d_hi) * 18446744073709551616.0f + u64_to_f32(d_lo)) / fc;
+        const float spread = u64_to_f32(spread_sum), spread_n = (float)spread_cnt;
+        const float lg = log2f(nnz_sm > 1 ? nz : 1.0f);
+        // numerator and denominator of this lane's quotient (0 / 1 where it has none)
         float num = 0.0f, den = 1.0f;
-        switch (j) {
-            case 2: num = nnz; den = (float)m * (float)n; break;
-            case 5: num = nnz; den = (float)m; break;
-            case 7: num = tot.sum_len > 0 ? sd : 0.0f; den = tot.sum_len > 0 ? mean : 1.0f; break;
-            case 9: num = tot.max_len > 0 ? mean : 0.0f; den = tot.max_len > 0 ? (float)tot.max_len : 1.0f; break;
-            case 10: num = tot.sum_len > 0 ? (float)(tot.sum_len - upto_k) : 0.0f; den = tot.sum_len > 0 ? L : 1.0f; break;
-            case 11: num = tot.spread_cnt > 0 ? (float)tot.spread_sum : 0.0f; den = tot.spread_cnt > 0 ? (float)tot.spread_cnt : 1.0f; break;
-            case 13: num = (float)tot.empty; den = fc; break;
-            case 14: num = (float)tot.longc; den = fc; break;
-            case 15: num = widths > 0 ? (float)capped_sum : 1.0f; den = widths > 0 ? 32.0f * (float)widths : 1.0f; break;
-            default: break;
+        num = j == 2 || j == 5 ? nz : num;
+        den = j == 2 ? (float)m * (float)n : den;
+        den = j == 5 ? (float)m : den;
+        num = j == 7 ? (sum_len > 0 ? sd : 0.0f) : num;
+        den = j == 7 ? (sum_len > 0 ? mean : 1.0f) : den;
+        num = j == 9 ? (max_len > 0 ? mean : 0.0f) : num;
+        den = j == 9 ? (max_len > 0 ? (float)max_len : 1.0f) : den;
+        num = j == 11 ? (spread_cnt > 0 ? spread : 0.0f) : num;
+        den = j == 11 ? (spread_cnt > 0 ? spread_n : 1.0f) : den;
+        num = j == 13 ? (float)empty : num;
+        num = j == 14 ? (float)longc : num;
+        den = j == 13 || j == 14 ? fc : den;
+        tail_sync();  // the scans' operands are in qop
+        num = j == 10 ? qop[0] : num;
+        den = j == 10 ? qop[1] : den;
+        num = j == 15 ? qop[2] : num;
+        den = j == 15 ? qop[3] : den;
+        f = num / den;
+        f = j == 0 ? (float)m : f;
+        f = j == 1 ? (float)n : f;
+        f = j == 3 ? (float)min_len : f;
+        f = j == 4 ? (float)max_len : f;
+        f = j == 6 ? sd : f;
+        f = j == 8 ? lg : f;
+        f = j == 12 ? (float)bandw : f;
+        if (lane < 16) {
+            if (feat_out) feat_out[lane] = f;
+            if (model_params) xs[lane] = feat_scale(lane, f, wsm + kNP + 3, wsm + kNP + 3 + 16);
         }
-        const float q = num / den;
-        const float lg = log2f(nnz > 1.0f ? nnz : 1.0f);
-        float f = q;
-        if (j == 0) f = (float)m;
-        if (j == 1) f = (float)n;
-        if (j == 3) f = (float)tot.min_len;
-        if (j == 4) f = (float)tot.max_len;
-        if (j == 6) f = sd;
-        if (j == 8) f = lg;
-        if (j == 12) f = (float)tot.band;
-        fs[j] = f;
-    }
-    tail_sync();
-    if (feat_out && tid < 16) feat_out[tid] = fs[tid];
-    if (model_params) {
-        if (tid < 16) xs[tid] = feat_scale(tid, fs[tid], wsm + kNP + 3, wsm + kNP + 3 + 16);
+    } else {
         tail_sync();
-        mlp_forward_64(wsm, xs, h1, h2, z);
-        if (tid == 0) {
-            int best = 0;
-            for (int c = 1; c < 5; ++c)
-                if (z[c] > z[best]) best = c;
-            if (fmt_out) fmt_out[0] = best;
-        }
-        if (logits_out && tid < 5) logits_out[tid] = z[tid];
     }
+    if (!model_params) return;
+    tail_sync();
+    const int best = mlp_forward_64(wsm, xs, h1, h2, logits_out);
+    if (tid == 0 && fmt_out) fmt_out[0] = best;
+}
+
+template <int CTAS, bool VEC>
+static cudaError_t launch_features_k(const spmv_csr* c, float* feat, const spmv_model* model, int32_t* fmt,
+                                     float* logits, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CTAS, 1, 1);
+    cfg.blockDim = dim3(kSample / CTAS, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CTAS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_features<CTAS, VEC>, c->ptr, c->idx, c->m, c->n, (int64_t)c->nnz, feat,
+                              model ? (const float*)model->params : nullptr, model ? (const float*)model->lo : nullptr,
+                              model ? (const float*)model->hi : nullptr, fmt, logits);
+}
+
+// The cluster size for this device: 16 CTAs (a non-portable size, opted into
+// here) where one such cluster can be resident, else the portable 8.  Both
+// give the same features bit for bit (exact integer statistics, the same FP32
+// code after them).  Cached per device.
+static int features_ctas() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kFeatCtasSmall;
+    if (cached[dev]) return cached[dev];
+    int ctas = kFeatCtasSmall;
+    if (cudaFuncSetAttribute(k_features<kFeatCtasLarge, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_features<kFeatCtasLarge, false>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kFeatCtasLarge, 1, 1);
+        cfg.blockDim = dim3(kSample / kFeatCtasLarge, 1, 1);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kFeatCtasLarge;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_features<kFeatCtasLarge, true>, &cfg) == cudaSuccess &&
+            clusters >= 1)
+            ctas = kFeatCtasLarge;
+    }
+    (void)cudaGetLastError();  // a refused opt-in leaves the portable size
+    cached[dev] = ctas;
+    return ctas;
 }
 
 static int launch_features(const spmv_csr* c, float* feat, const spmv_model* model, int32_t* fmt, float* logits,
                            cudaStream_t s) {
     if (!c) return set_error(SPMV_ERR_INVALID_ARG, "csr is NULL");
-    if (c->m <= 0 || c->n <= 0 || !c->ptr || (c->nnz > 0 && !c->idx))
+    if (c->m <= 0 || c->n <= 0 || !c->ptr || (c->nnz > 0 && !c->idx) || c->nnz < 0)
         return set_error(SPMV_ERR_INVALID_ARG, "malformed csr argument");
-    k_features<<<kFeatCtas, kFeatThreads, 0, s>>>(c->ptr, c->idx, c->m, c->n, feat, model ? model->params : nullptr,
-                                                 model ? model->lo : nullptr, model ? model->hi : nullptr, fmt, logits);
-    SPMV_CUDA(cudaGetLastError());
+    const bool vec = (reinterpret_cast<uintptr_t>(c->idx) & 15) == 0;
+    const bool large = features_ctas() == kFeatCtasLarge;
+    const cudaError_t e = large ? (vec ? launch_features_k<kFeatCtasLarge, true>(c, feat, model, fmt, logits, s)
+                                       : launch_features_k<kFeatCtasLarge, false>(c, feat, model, fmt, logits, s))
+                                : (vec ? launch_features_k<kFeatCtasSmall, true>(c, feat, model, fmt, logits, s)
+                                       : launch_features_k<kFeatCtasSmall, false>(c, feat, model, fmt, logits, s));
+    SPMV_CUDA(e);
     return SPMV_OK;
 }
 
