@@ -168,9 +168,14 @@ SPMV_API void spmv_free(spmv_handle* h);
 /* ------------------------------------------------- features and selection */
 
 /* The 16 static features of Sec. V-B (Table IV's eight plus eight more) as
- * float32 into feat_dev[16]; see the feature definitions in the library's
- * documentation.  One kernel launch, asynchronous.  Rows are sampled (at most
- * 16384) so the cost does not grow with M. */
+ * float32 into feat_dev[16] (device memory): 0 n_rows, 1 n_cols, 2 nnz/(M*N),
+ * 3 min, 4 max, 5 mean, 6 std of the row length, 7 std/mean, 8 log2 nnz,
+ * 9 mean/max, 10 HYB tail fraction, 11 mean and 12 max |col - row| over each
+ * row's first 16 entries, 13 empty-row fraction, 14 fraction of rows of length
+ * >= 32, 15 SELL-32 fill; the statistics are over rows floor(k*M/8192),
+ * k < 8192, when M > 8192 (all rows otherwise), so the cost does not grow
+ * with M.  csr->idx holds csr->nnz entries and needs no particular alignment.
+ * One kernel launch (a thread-block cluster), asynchronous. */
 SPMV_API int spmv_features(const spmv_csr* csr, float* feat_dev, cudaStream_t stream);
 
 /* A trained selector: network parameters (SPMV_MLP_PARAMS floats, W1, b1, W2,
@@ -282,6 +287,13 @@ SPMV_API int spmv_probe_gather(const int32_t* idx, const double* val, int64_t nn
 /* Make the k-th device allocation from now fail with SPMV_ERR_ALLOC
  * (k >= 1; 0 disables).  For testing error paths; process-wide. */
 SPMV_API void spmv_debug_fail_alloc(int32_t k);
+
+/* Force the cluster size of the features kernel: 8 or 16 CTAs (0 restores the
+ * automatic choice: 16 where the device can place such a cluster, else 8).
+ * Both sizes compute the same features bit for bit; this lets a test run
+ * each.  Process-wide.  A forced size the device cannot place makes the
+ * features calls return SPMV_ERR_CUDA. */
+SPMV_API void spmv_debug_features_cluster(int32_t ctas);
 
 #ifdef __cplusplus
 }

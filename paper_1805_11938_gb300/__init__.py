@@ -26,7 +26,7 @@ __all__ = [
     "SpmvError", "DeviceCSR", "Handle", "Model", "Batch", "spmv_convert", "spmv_run", "spmv_to_csr",
     "spmv_features", "spmv_select", "spmv_select_async", "spmv_mlp_scale", "spmv_mlp_loss_grad", "spmv_mlp_adam",
     "spmv_mlp_train", "spmv_mlp_forward", "spmv_batch_build", "spmv_batch_run", "spmv_batch_run_separate",
-    "spmv_csr_run_noalloc", "spmv_debug_fail_alloc", "spmv_probe_gather", "lib",
+    "spmv_csr_run_noalloc", "spmv_debug_fail_alloc", "spmv_debug_features_cluster", "spmv_probe_gather", "lib",
 ]
 
 
@@ -323,6 +323,10 @@ def spmv_csr_run_noalloc(csr: DeviceCSR, x, y=None, stream=None):
 
 def spmv_debug_fail_alloc(k: int) -> None:
     lib().spmv_debug_fail_alloc(int(k))
+
+
+def spmv_debug_features_cluster(ctas: int) -> None:
+    lib().spmv_debug_features_cluster(int(ctas))
 
 
 def spmv_probe_gather(csr: DeviceCSR, x, partial=None, stream=None):

@@ -9,6 +9,7 @@ namespace spmv {
 const char* last_error();
 void clear_error();
 void debug_fail_alloc(int k);
+void debug_features_cluster(int ctas);
 }  // namespace spmv
 
 using namespace spmv;
@@ -34,6 +35,8 @@ const char* spmv_strerror(int status) {
 const char* spmv_last_error(void) { return last_error(); }
 
 void spmv_debug_fail_alloc(int32_t k) { debug_fail_alloc(k); }
+
+void spmv_debug_features_cluster(int32_t ctas) { debug_features_cluster(ctas); }
 
 int spmv_convert(spmv_fmt fmt, const spmv_csr* csr, const spmv_params* params, cudaStream_t stream,
                  spmv_handle** out) {

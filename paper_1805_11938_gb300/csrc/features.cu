@@ -21,6 +21,7 @@
 // then, for a selection, both run the network.  A lone warp's dependent
 // instructions are the cost there, so that code avoids divergent per-feature
 // branches and keeps its divisions independent.
+#include <atomic>
 #include <cooperative_groups.h>
 #include <cuda_pipeline.h>
 
@@ -447,11 +448,14 @@ static cudaError_t launch_features_k(const spmv_csr* c, float* feat, const spmv_
 // here) where one such cluster can be resident, else the portable 8.  Both
 // give the same features bit for bit (exact integer statistics, the same FP32
 // code after them).  Cached per device.
+static std::atomic<int> g_force_ctas{0};
+
 static int features_ctas() {
     static int cached[64] = {0};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kFeatCtasSmall;
-    if (cached[dev]) return cached[dev];
+    const int forced = g_force_ctas.load();
+    if (cached[dev]) return forced ? forced : cached[dev];
     int ctas = kFeatCtasSmall;
     if (cudaFuncSetAttribute(k_features<kFeatCtasLarge, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess &&
@@ -474,7 +478,11 @@ static int features_ctas() {
     }
     (void)cudaGetLastError();  // a refused opt-in leaves the portable size
     cached[dev] = ctas;
-    return ctas;
+    return forced ? forced : ctas;
+}
+
+void debug_features_cluster(int ctas) {
+    g_force_ctas.store(ctas == kFeatCtasSmall || ctas == kFeatCtasLarge ? ctas : 0);
 }
 
 static int launch_features(const spmv_csr* c, float* feat, const spmv_model* model, int32_t* fmt, float* logits,

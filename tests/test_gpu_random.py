@@ -93,3 +93,40 @@ def test_random_matrices_features(sp, seed):
     f = sp.spmv_features(sp.DeviceCSR.from_host(a)).cpu().numpy()
     ref = oracle.features(a).astype(np.float32)
     assert np.allclose(f, ref, rtol=2e-6, atol=0), (a.name, np.stack([f, ref]))
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_features_cluster_sizes_and_unaligned_idx(sp, seed):
+    """The features kernel's two cluster sizes (8 and 16 CTAs), and its scalar
+    index loads (idx not 16-byte aligned) beside the 16-byte ones, give the
+    same features bit for bit and the same selection, within the oracle's
+    tolerance."""
+    rng = np.random.default_rng(7000 + seed)
+    m = int(rng.choice([5, 8191, 8192, 8193, int(rng.integers(9000, 80_000))]))
+    n = int(rng.integers(1, 100_000))
+    lens = np.where(rng.random(m) < 0.2, 0, rng.integers(1, 40, size=m))
+    lens[rng.random(m) < 0.01] = 700
+    lens[-1] = 3  # the last row ends at the end of idx: its 16-byte words run past it
+    ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    a = synth.CSR(m, n, ptr, rng.integers(0, n, size=int(ptr[-1])).astype(np.int32), np.ones(int(ptr[-1])),
+                  f"cluster{seed}")
+    d = sp.DeviceCSR.from_host(a)
+    idx_pad = torch.zeros(a.nnz + 1, dtype=torch.int32, device="cuda")
+    idx_pad[1:] = d.idx
+    du = sp.DeviceCSR(a.m, a.n, d.ptr, idx_pad[1:], d.val)
+    assert du.idx.data_ptr() % 16 != 0
+    model = sp.Model.load(sp.MODEL_PATH)
+    outs, sels = [], []
+    try:
+        for ctas in (0, 8, 16):
+            sp.spmv_debug_features_cluster(ctas)
+            for dd in (d, du):
+                outs.append(sp.spmv_features(dd).cpu().numpy())
+                sels.append(sp.spmv_select(dd, model))
+    finally:
+        sp.spmv_debug_features_cluster(0)
+    for f in outs[1:]:
+        assert np.array_equal(f.view(np.uint32), outs[0].view(np.uint32)), (a.name, np.stack([f, outs[0]]))
+    assert len(set(sels)) == 1, sels
+    ref = oracle.features(a).astype(np.float32)
+    assert np.allclose(outs[0], ref, rtol=2e-6, atol=0), (a.name, np.stack([outs[0], ref]))
