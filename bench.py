@@ -3,10 +3,12 @@
 
 One step = the deployment path on one matrix resident in HBM: the selector
 kernel (features + scaling + network, result kept on the device) and the
-product y = A x in the format the selector chose for this matrix.  Every
-format is also timed on its own; conversions are timed once.  Between timed
-steps a 256 MiB buffer is written to flush L2, and each step is bracketed by
-CUDA events on the stream the kernels run on.
+product y = A x in the format the selector chose for this matrix.  The
+step's two kernels are captured once as a CUDA graph that every timed step
+replays (--no-graph launches them directly).  Every format is also timed on
+its own; conversions are timed once.  Between timed steps a 256 MiB buffer is
+written to flush L2, and each step is bracketed by CUDA events on the stream
+the kernels run on.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...     # the CPU oracle on the host cores
@@ -398,6 +400,7 @@ def main():
     ap.add_argument("--formats", default="0,1,2,3,4")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-format", type=int, default=-1, help="batch512: one format for every matrix (-1: selector)")
+    ap.add_argument("--no-graph", action="store_true", help="launch the timed steps directly instead of replaying a CUDA graph")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -526,29 +529,55 @@ def main():
         select_step()
         sp.spmv_run(hc, x, y)
 
-    # ---- timed steps (the headline)
+    # ---- timed steps (the headline).  The step's two launches (the selector
+    # kernel, the product) are captured once as a CUDA graph and the graph is
+    # replayed every step: each replay runs both kernels in full, without the
+    # host between them.
     for _ in range(args.warmup):
         flush.zero_()
         step()
+    torch.cuda.synchronize()
+    graph = None
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            flush.zero_()
+            graph.replay()
+    run_step = graph.replay if graph is not None else step
     barrier()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         barrier()
         t_wall = time.perf_counter()
-        for s, mid, e in ev:
+        for s, e in ev:
             flush.zero_()
             s.record(stream)
-            select_step()
-            mid.record(stream)
-            sp.spmv_run(hc, x, y)
+            run_step()
             e.record(stream)
         barrier()
         t_wall = time.perf_counter() - t_wall
-    step_ms = [s.elapsed_time(e) for s, _, e in ev]
-    kern_ms = [m.elapsed_time(e) for _, m, e in ev]
+    step_ms = [s.elapsed_time(e) for s, e in ev]
     total_ms, value = reduce_over_ranks(sum(step_ms), 2.0 * a.nnz * args.steps, dist, "cuda")
     clocks = clk.summary()
+    # The product kernel's own duration for the roofline: the same steps once
+    # more, launched directly with an event between the two kernels (an event
+    # there delays the second launch by a few microseconds, so it stays out of
+    # the headline loop).
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s, mid, e in ev:
+        flush.zero_()
+        s.record(stream)
+        select_step()
+        mid.record(stream)
+        sp.spmv_run(hc, x, y)
+        e.record(stream)
+    torch.cuda.synchronize()
+    kern_ms = [m.elapsed_time(e) for _, m, e in ev]
+    eager_step_ms = statistics.mean(s.elapsed_time(e) for s, _, e in ev)
 
     # ---- end to end: every step copies its x in from pinned host memory, runs
     # the step through the library, and copies its y out.  x and y are
@@ -631,9 +660,13 @@ def main():
                    "selected_format": FORMATS[chosen], "exhaustive_best": FORMATS[best], "selector": selector_kind,
                    "selected_params": tuned_params, "tuning": tuning,
                    "step": "selector kernel + SpMV in the selected format, matrix and x resident in HBM",
+                   "launch": ("the step's two kernels captured once as a CUDA graph, replayed every step"
+                              if graph is not None else "the step's two kernels launched directly"),
+                   "direct_launch_step_ms": eager_step_ms,
                    "l2": "flushed: 256 MiB written before every timed step", "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": f"{FORMATS[chosen]} product", "kernel_ms": kms,
+                     "kernel_ms_source": "CUDA events around the product in a second pass of the same steps",
                      "alg_bytes_per_launch": ab, "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy, burst)",
                      "gather_ceiling": {"ms": probe_ms, "g_gathers_per_s": a.nnz / probe_ms / 1e6,
                                         "frac": probe_ms / kms,
