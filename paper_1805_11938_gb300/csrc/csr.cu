@@ -14,6 +14,7 @@ template <bool ADD>
 __global__ void __launch_bounds__(256) k_csr_tiles(dev::CsrArgs a) {
     extern __shared__ __align__(16) unsigned char csr_smem[];
     dev::CsrWarpSmem* S = reinterpret_cast<dev::CsrWarpSmem*>(csr_smem);
+    dev::pdl_wait();  // launched early (launch_pdl): wait for the kernel ahead
     const int w = threadIdx.x >> 5;
     const int32_t stride = (int32_t)gridDim.x * dev::kCsrWarps;
     for (int32_t t = (int32_t)blockIdx.x * dev::kCsrWarps + w; t < a.ntiles; t += stride)
@@ -21,6 +22,7 @@ __global__ void __launch_bounds__(256) k_csr_tiles(dev::CsrArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_csr_zero(dev::CsrArgs a) {
+    dev::pdl_wait();
     dev::csr_zero(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
@@ -52,10 +54,10 @@ int csr_tiles_launch(const CsrTiles& ct, const int32_t* ptr, const int32_t* idx,
                      const int32_t* row_map, const double* x, double* y, bool add, cudaStream_t s) {
     const dev::CsrArgs a = csr_tile_args(ct, ptr, idx, val, row_map, x, y);
     if (ct.n > 0) {
-        if (add) k_csr_tiles<true><<<ct.grid, 256, dev::kCsrSmemBytes, s>>>(a);
-        else k_csr_tiles<false><<<ct.grid, 256, dev::kCsrSmemBytes, s>>>(a);
+        if (add) launch_pdl(k_csr_tiles<true>, dim3(ct.grid), dim3(256), dev::kCsrSmemBytes, s, a);
+        else launch_pdl(k_csr_tiles<false>, dim3(ct.grid), dim3(256), dev::kCsrSmemBytes, s, a);
     } else if (!add && ct.rows > 0) {
-        k_csr_zero<<<grid_for(ct.rows, 256), 256, 0, s>>>(a);
+        launch_pdl(k_csr_zero, dim3(grid_for(ct.rows, 256)), dim3(256), 0, s, a);
     }
     SPMV_CUDA(cudaGetLastError());
     return SPMV_OK;

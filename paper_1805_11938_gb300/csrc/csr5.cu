@@ -203,11 +203,13 @@ int csr5_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
 }
 
 __global__ void __launch_bounds__(256) k_csr5(dev::Csr5Args a) {
+    dev::pdl_wait();  // launched early (launch_pdl): wait for the kernel ahead
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (t < a.ntiles) dev::csr5_tile(a, t, threadIdx.x & 31);
 }
 
 __global__ void __launch_bounds__(256) k_csr5_zero(dev::Csr5Args a) {
+    dev::pdl_wait();
     dev::csr5_zero_all(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x);
 }
 
@@ -219,8 +221,8 @@ dev::Csr5Args csr5_args(const spmv_handle* h, const double* x, double* y) {
 
 int csr5_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s) {
     const dev::Csr5Args a = csr5_args(h, x, y);
-    if (h->ntiles > 0) k_csr5<<<grid_for(h->ntiles * 32, 256), 256, 0, s>>>(a);
-    else if (h->n_zero_rows > 0) k_csr5_zero<<<grid_for(h->n_zero_rows, 256), 256, 0, s>>>(a);
+    if (h->ntiles > 0) launch_pdl(k_csr5, dim3(grid_for(h->ntiles * 32, 256)), dim3(256), 0, s, a);
+    else if (h->n_zero_rows > 0) launch_pdl(k_csr5_zero, dim3(grid_for(h->n_zero_rows, 256)), dim3(256), 0, s, a);
     SPMV_CUDA(cudaGetLastError());
     return SPMV_OK;
 }

@@ -111,6 +111,7 @@ int ell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
 // Blocks [0, nb) take 512 rows each (2 per thread); blocks nb.. take one long row each.
 __global__ void __launch_bounds__(256) k_ell(dev::EllArgs a, int32_t nb, const int32_t* __restrict__ long_rows) {
     __shared__ double red[8];
+    dev::pdl_wait();  // launched early (launch_pdl): wait for the kernel ahead
     if ((int32_t)blockIdx.x < nb) {
         dev::ell_rows2(a, (int32_t)(blockIdx.x * 512 + threadIdx.x * 2));
     } else {
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(256) k_ell(dev::EllArgs a, int32_t nb, const i
 int ell_launch(const EllPart& e, int32_t m, int32_t long_len, const double* x, double* y, cudaStream_t s) {
     dev::EllArgs a{e.row_len, e.col, e.val, e.ld, m, long_len, x, y};
     const int32_t nb = (int32_t)ceil_div(m, 512);
-    k_ell<<<nb + e.n_long, 256, 0, s>>>(a, nb, e.long_rows);
+    launch_pdl(k_ell, dim3(nb + e.n_long), dim3(256), 0, s, a, nb, e.long_rows);
     SPMV_CUDA(cudaGetLastError());
     return SPMV_OK;
 }

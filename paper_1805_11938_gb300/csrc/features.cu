@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(kSample / CTAS)
     __shared__ int32_t nnz_sm;
     __shared__ __align__(16) float xs[16], h1[64], h2[64];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    dev::pdl_trigger();  // a product launched behind this kernel may get resident now
     // CTA 0 starts copying what its tail needs into shared memory now
     // (asynchronous copies, waited for just before the tail): nnz = ptr[m]
     // and, for a selection, the network and the scaling table.

@@ -216,4 +216,25 @@ inline int grid_for(int64_t n, int per_block) {
     return (int)(g < 1 ? 1 : (g > 0x7fffffff ? 0x7fffffff : g));
 }
 
+// Launch with programmatic stream serialization: the kernel's blocks may get
+// resident while the kernel ahead of it in the stream is still finishing
+// (that kernel lets them in with dev::pdl_trigger(), or simply by ending).
+// Every kernel launched this way calls dev::pdl_wait() before it touches
+// memory, which returns once the kernel ahead has completed and its writes
+// are visible, so stream order is kept.
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 }  // namespace spmv

@@ -16,6 +16,14 @@ namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start before the kernel ahead of it in the stream has
+// finished; pdl_wait() blocks until that kernel has completed and its memory
+// is visible (a no-op for an ordinary launch).  pdl_trigger() lets the next
+// such kernel start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ double ldx(const double* x, int32_t c) { return __ldg(x + c); }
 
 // Row of nonzero k: the largest i with ptr[i] <= k (empty rows are skipped).

@@ -328,6 +328,7 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
 // C = 32 on the power-law matrix 77.6 us at 40 registers, 74.8 at 32).
 template <int R, bool ADD>
 __global__ void __launch_bounds__(256, R == 1 ? 8 : (R == 2 ? 5 : 4)) k_sell(dev::SellArgs a, int32_t nu) {
+    dev::pdl_wait();  // launched early (launch_pdl): wait for the kernel ahead
     const int32_t stride = (int32_t)gridDim.x * 8;
     for (int32_t u = (int32_t)(blockIdx.x * 8 + (threadIdx.x >> 5)); u < nu; u += stride)
         dev::sell_unit<R, ADD>(a, u, threadIdx.x & 31);
@@ -357,9 +358,18 @@ static void sell_launch(const spmv_handle* h, const double* x, double* y, cudaSt
     if (h->n_sell_units <= 0) return;
     const int64_t need = grid_for(h->n_sell_units, 8);
     switch (h->sell_C) {
-        case 32: k_sell<1, ADD><<<(int)std::min<int64_t>(need, sell_grid<1>()), 256, 0, s>>>(a, h->n_sell_units); break;
-        case 64: k_sell<2, ADD><<<(int)std::min<int64_t>(need, sell_grid<2>()), 256, 0, s>>>(a, h->n_sell_units); break;
-        default: k_sell<4, ADD><<<(int)std::min<int64_t>(need, sell_grid<4>()), 256, 0, s>>>(a, h->n_sell_units); break;
+        case 32:
+            launch_pdl(k_sell<1, ADD>, dim3((unsigned)std::min<int64_t>(need, sell_grid<1>())), dim3(256), 0, s, a,
+                       h->n_sell_units);
+            break;
+        case 64:
+            launch_pdl(k_sell<2, ADD>, dim3((unsigned)std::min<int64_t>(need, sell_grid<2>())), dim3(256), 0, s, a,
+                       h->n_sell_units);
+            break;
+        default:
+            launch_pdl(k_sell<4, ADD>, dim3((unsigned)std::min<int64_t>(need, sell_grid<4>())), dim3(256), 0, s, a,
+                       h->n_sell_units);
+            break;
     }
 }
 
