@@ -344,10 +344,22 @@ def run_batch(args, rank: int, world: int) -> None:
     tb = statistics.mean(t_b)
     ts = statistics.mean(t_s)
     total_b, value = reduce_over_ranks(sum(t_b), 2.0 * total_nnz * args.steps, dist, "cuda")
-    # kernels per replay: the plain task kinds, the CSR tiles (CSR matrices and HYB tails), the HYB tails
-    has_tail = any(i["fmt"] == 4 and i["aux"][1] > 0 for i in infos)
-    launches_per_replay = (int(any(i["fmt"] != 0 or i["nnz"] == 0 for i in infos))
-                           + int(any(i["fmt"] == 0 and i["nnz"] > 0 for i in infos)) + int(has_tail))
+    # kernels per replay: one persistent kernel per non-empty task family, as the
+    # library groups them (CSR5, ELL, ELL parts of HYB and empty CSR; SELL by
+    # chunk size C = 32, 64, 128; CSR tiles; HYB tails)
+    families = set()
+    for i in infos:
+        f, aux = i["fmt"], i["aux"]
+        if f == 0:
+            families.add("csr" if aux[0] > 0 else "other")
+        elif f == 3:
+            if aux[1] > 0:
+                families.add({32: "sell32", 64: "sell64"}.get(i["params"]["sell_C"], "sell128"))
+        else:
+            families.add("other")
+            if f == 4 and aux[1] > 0:
+                families.add("hyb_tail")
+    launches_per_replay = len(families)
     ab = sum(algorithmic_bytes(i["fmt"], i) for i in infos)
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -355,6 +367,11 @@ def run_batch(args, rank: int, world: int) -> None:
         with open(pk) as fh:
             peaks = json.load(fh)
     peak = peaks.get("hbm_gbs") or 6800.0
+    batch_traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path) and args.batch_format < 0:
+        with open(tr_path) as fh:
+            batch_traffic = json.load(fh).get(f"batch{n_mat}:{os.path.basename(model_path)}")
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_b / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -364,7 +381,9 @@ def run_batch(args, rank: int, world: int) -> None:
                        "l2": "flushed: 256 MiB written before every timed step", "setup_s": t_setup,
                        "step": "one graph replay of the persistent batched kernel over all matrices"},
             "roofline": {"bound": "hbm", "achieved": ab / tb / 1e6, "peak": peak, "unit": "GB/s",
-                         "frac": ab / tb / 1e6 / peak, "traffic": None, "kernel": "persistent batched product",
+                         "frac": ab / tb / 1e6 / peak, "traffic": batch_traffic,
+                         "kernel": f"persistent batched product ({launches_per_replay} family kernels per replay: "
+                                   f"{', '.join(sorted(families))}); traffic summed over them",
                          "alg_bytes_per_launch": ab},
             "batched_ms": tb, "separate_ms": ts, "batched_speedup_over_separate": ts / tb,
             "separate_gflops": 2.0 * total_nnz / ts / 1e6, "bitwise_equal_to_separate": same,
