@@ -104,6 +104,26 @@ def launches_per_run(fmt: int, info: dict) -> int:
     return 1
 
 
+def batch_families(infos) -> set:
+    """Task families of a batch (include/spmv.h, spmv_batch_build): one
+    persistent kernel per family present runs in each replay.  CSR5, ELL, the
+    ELL part of HYB and CSR without nonzeros share one family; SELL has one
+    per chunk size C = 32, 64, 128; CSR tiles and HYB tails have their own."""
+    families = set()
+    for i in infos:
+        f, aux = i["fmt"], i["aux"]
+        if f == 0:
+            families.add("csr" if aux[0] > 0 else "other")
+        elif f == 3:
+            if aux[1] > 0:
+                families.add({32: "sell32", 64: "sell64"}.get(i["params"]["sell_C"], "sell128"))
+        else:
+            families.add("other")
+            if f == 4 and aux[1] > 0:
+                families.add("hyb_tail")
+    return families
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -344,21 +364,7 @@ def run_batch(args, rank: int, world: int) -> None:
     tb = statistics.mean(t_b)
     ts = statistics.mean(t_s)
     total_b, value = reduce_over_ranks(sum(t_b), 2.0 * total_nnz * args.steps, dist, "cuda")
-    # kernels per replay: one persistent kernel per non-empty task family, as the
-    # library groups them (CSR5, ELL, ELL parts of HYB and empty CSR; SELL by
-    # chunk size C = 32, 64, 128; CSR tiles; HYB tails)
-    families = set()
-    for i in infos:
-        f, aux = i["fmt"], i["aux"]
-        if f == 0:
-            families.add("csr" if aux[0] > 0 else "other")
-        elif f == 3:
-            if aux[1] > 0:
-                families.add({32: "sell32", 64: "sell64"}.get(i["params"]["sell_C"], "sell128"))
-        else:
-            families.add("other")
-            if f == 4 and aux[1] > 0:
-                families.add("hyb_tail")
+    families = batch_families(infos)
     launches_per_replay = len(families)
     ab = sum(algorithmic_bytes(i["fmt"], i) for i in infos)
     peaks = {}

@@ -226,10 +226,11 @@ SPMV_API int spmv_mlp_forward(const float* theta_dev, const float* X_dev, int32_
 /* ------------------------------------------------------------- batching */
 
 /* Many independent products y_b = A_b x_b in one CUDA graph of persistent
- * launches (CSR tiles and HYB tails in one kernel, the other formats in
- * another).  build lays out the work lists over all handles (each keeps its
- * own format) and captures the launches on a stream of its own; the handles
- * must outlive the batch.  A SELL handle in column panels is refused
+ * launches, one per task family present: CSR5, ELL, the ELL part of HYB and
+ * CSR without nonzeros; SELL with C = 32; with C = 64; with C = 128; CSR
+ * tiles; HYB tails.  build lays out the work lists over all handles (each
+ * keeps its own format) and captures the launches on a stream of its own; the
+ * handles must outlive the batch.  A SELL handle in column panels is refused
  * (INVALID_ARG): its panels must run one after another.  Synchronises. */
 SPMV_API int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t stream, spmv_batch** out);
 
