@@ -35,10 +35,12 @@ def _feature_cases():
         synth.from_lengths_random_cols(lens, 800, 8, "empty_mix"),
         synth.tiny_random(3, 2, 0.5, 9),
         synth.uniform_random(40_000, 600, 10),            # every row longer than the 512 cap
+        synth.from_lengths_random_cols(np.zeros(50, np.int32), 10, 11, "all_empty"),  # nnz = 0, idx NULL
+        synth.from_lengths_random_cols(np.zeros(20_000, np.int32), 10, 12, "all_empty_sampled"),
     ]
 
 
-@pytest.mark.parametrize("ci", range(9))
+@pytest.mark.parametrize("ci", range(11))
 def test_features_match_oracle(ci):
     a = _feature_cases()[ci]
     f = sp.spmv_features(sp.DeviceCSR.from_host(a)).cpu().numpy()
