@@ -51,9 +51,9 @@ constexpr int oW1 = 0, oB1 = 1024, oW2 = 1088, oB2 = 5184, oW3 = 5248, oB3 = 556
 // FP64 pipe makes double log2/division/sqrt several microseconds slower, and
 // the features are float32 values to begin with.  Both logarithms are taken
 // and one is selected, so lanes scaling different features do not diverge.
-// Quotients here and in the features use the two-ulp division (reciprocal and
-// multiply, no branch to a slow path), so independent ones overlap; every
-// operand lies far inside its range.
+// The scaling's quotient uses the two-ulp division (reciprocal and multiply,
+// no branch to a slow path); its operands lie far inside that division's
+// range.  The features themselves keep correctly rounded divisions.
 __device__ __forceinline__ float feat_transform(int j, float f) {
     constexpr unsigned kLog1p = (1u << 0) | (1u << 1) | (1u << 3) | (1u << 4) | (1u << 5) | (1u << 6) | (1u << 11) |
                                 (1u << 12);
