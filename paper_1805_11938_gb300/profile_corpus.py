@@ -22,7 +22,14 @@ Each matrix is timed twice per format:
 One JSON line per matrix is appended to the output file, so an interrupted run
 resumes where it stopped (matrices already in the file are skipped).
 
-    python -m paper_1805_11938_gb300.profile_corpus --out table.jsonl [--count 1000]
+--classes 7 times two more candidates beside the five formats, both from
+Sec. II/III of the paper and both settings of the library's kernels: plain
+SELL (SELL-C-sigma with sigma = 1, no sorting) and the standalone COO format
+(HYB with every entry in its COO part, which the library stores grouped by
+row).  Such a table names its classes in each line ("classes"); the shipped
+selectors keep the five formats.
+
+    python -m paper_1805_11938_gb300.profile_corpus --out table.jsonl [--count 1000] [--classes 7]
 """
 from __future__ import annotations
 
@@ -38,6 +45,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FORMAT_CAP_BYTES = 24 << 30  # a padded layout larger than this counts as infeasible (throughput 0)
+HYB_K_NONE = -1              # hyb_k: every entry in the COO part (include/spmv.h SPMV_HYB_K_NONE)
+# candidate classes: (name, format id, conversion parameters)
+CLASSES_5 = [("CSR", 0, {}), ("CSR5", 1, {}), ("ELL", 2, {}), ("SELL", 3, {}), ("HYB", 4, {})]
+CLASSES_7 = CLASSES_5 + [("SELL_plain", 3, {"sell_sigma": 1}), ("COO", 4, {"hyb_k": HYB_K_NONE})]
 REPLICA_NNZ = 1 << 23        # nonzeros of the block-diagonal replica used for the throughput time
 
 
@@ -75,57 +86,61 @@ def done_indices(path: str) -> set:
     return out
 
 
-def _time_formats(a, seed, timer, cap_bytes, measure_kw):
+def _time_formats(a, seed, timer, cap_bytes, measure_kw, classes=CLASSES_5):
     import torch
 
     import synth
-    from . import FORMATS, DeviceCSR, SpmvError, spmv_convert, spmv_run
+    from . import DeviceCSR, SpmvError, spmv_convert, spmv_run
 
     d = DeviceCSR.from_host(a)
     x = torch.as_tensor(synth.vector(a.n, seed ^ 0x77)).cuda()
     y = torch.empty(a.m, dtype=torch.float64, device="cuda")
     times, status, conv = {}, {}, {}
-    for f in range(5):
+    for name, f, params in classes:
         try:
             t0 = time.perf_counter()
-            h = spmv_convert(f, d, {"max_bytes": cap_bytes})
+            h = spmv_convert(f, d, {"max_bytes": cap_bytes, **params})
             torch.cuda.synchronize()
-            conv[FORMATS[f]] = 1e3 * (time.perf_counter() - t0)
+            conv[name] = 1e3 * (time.perf_counter() - t0)
         except SpmvError as e:
-            times[FORMATS[f]] = None
-            status[FORMATS[f]] = e.name
+            times[name] = None
+            status[name] = e.name
             continue
         r = timer.measure(lambda: spmv_run(h, x, y), **measure_kw)
-        times[FORMATS[f]] = r["ms"]
-        status[FORMATS[f]] = f"ci={r['ci_halfwidth_ms'] / r['ms']:.3f} n={r['n']}"
+        times[name] = r["ms"]
+        status[name] = f"ci={r['ci_halfwidth_ms'] / r['ms']:.3f} n={r['n']}"
         del h
     return d, times, status, conv
 
 
-def profile_one(a, spec, timer, cap_bytes: int, measure_kw: dict) -> dict:
-    from . import FORMATS, spmv_features
+def profile_one(a, spec, timer, cap_bytes: int, measure_kw: dict, classes=CLASSES_5) -> dict:
+    from . import spmv_features
 
-    d, times, status, conv = _time_formats(a, spec["seed"], timer, cap_bytes, measure_kw)
+    names = [c[0] for c in classes]
+    d, times, status, conv = _time_formats(a, spec["seed"], timer, cap_bytes, measure_kw, classes)
     feat = spmv_features(d).cpu().numpy().astype(float).tolist()
     del d
     k = replica_count(a)
     if k == 1:
         times_b = dict(times)
     else:
-        _, tb, _, _ = _time_formats(replica(a, k), spec["seed"], timer, cap_bytes, measure_kw)
+        _, tb, _, _ = _time_formats(replica(a, k), spec["seed"], timer, cap_bytes, measure_kw, classes)
         times_b = {f: (None if v is None else v / k) for f, v in tb.items()}
     feas = {f: v for f, v in times.items() if v is not None}
     best = min(feas, key=lambda f: feas[f])
     feas_b = {f: v for f, v in times_b.items() if v is not None}
     best_b = min(feas_b, key=lambda f: feas_b[f])
-    return {"index": spec["index"], "spec": {k2: v for k2, v in spec.items() if k2 != "seed"}, "m": a.m, "nnz": a.nnz,
-            "features": feat, "ms": times, "status": status, "convert_ms": conv, "label": FORMATS.index(best),
-            "best": best, "replicas": k, "ms_batch": times_b, "label_batch": FORMATS.index(best_b),
-            "best_batch": best_b}
+    rec = {"index": spec["index"], "spec": {k2: v for k2, v in spec.items() if k2 != "seed"}, "m": a.m, "nnz": a.nnz,
+           "features": feat, "ms": times, "status": status, "convert_ms": conv, "label": names.index(best),
+           "best": best, "replicas": k, "ms_batch": times_b, "label_batch": names.index(best_b),
+           "best_batch": best_b}
+    if classes is not CLASSES_5:
+        rec["classes"] = names
+    return rec
 
 
 def run(out: str, count: int = 1000, start: int = 0, cap_bytes: int = FORMAT_CAP_BYTES, n_min: int = 10,
-        n_max: int = 60, log=print) -> None:
+        n_max: int = 60, log=print, classes=CLASSES_5) -> None:
     import synth
     from .autotune import Timer
 
@@ -142,7 +157,7 @@ def run(out: str, count: int = 1000, start: int = 0, cap_bytes: int = FORMAT_CAP
             a = futs.pop(i).result()
             if j + 2 < len(todo):
                 futs[todo[j + 2]] = ex.submit(synth.corpus_matrix, todo[j + 2])
-            rec = profile_one(a, synth.corpus_spec(i), timer, cap_bytes, kw)
+            rec = profile_one(a, synth.corpus_spec(i), timer, cap_bytes, kw, classes)
             fh.write(json.dumps(rec) + "\n")
             fh.flush()
             if j % 50 == 0:
@@ -156,8 +171,10 @@ def main():
     ap.add_argument("--count", type=int, default=1000)
     ap.add_argument("--start", type=int, default=0)
     ap.add_argument("--cap-gb", type=float, default=24.0)
+    ap.add_argument("--classes", type=int, default=5, choices=(5, 7))
     args = ap.parse_args()
-    run(args.out, args.count, args.start, int(args.cap_gb * (1 << 30)))
+    run(args.out, args.count, args.start, int(args.cap_gb * (1 << 30)),
+        classes=CLASSES_7 if args.classes == 7 else CLASSES_5)
 
 
 if __name__ == "__main__":

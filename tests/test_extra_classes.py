@@ -1,0 +1,51 @@
+"""The seven-class evaluation (plain SELL and COO beside the paper's five) on a
+synthetic table whose answers are known in closed form."""
+import numpy as np
+import pytest
+
+from paper_1805_11938_gb300 import extra_classes as ec
+from paper_1805_11938_gb300.train_selector import split
+
+NAMES = list(ec.BASE) + ["SELL_plain", "COO"]
+
+
+def test_best_and_pct():
+    ms = {"CSR": 3.0, "CSR5": 2.0, "ELL": None, "SELL": 4.0, "HYB": 5.0, "SELL_plain": 1.0, "COO": 6.0}
+    assert ec.best(ms, ec.BASE) == ("CSR5", 2.0)
+    assert ec.best(ms, NAMES) == ("SELL_plain", 1.0)
+    assert ec.pct_vs(ms, NAMES, "CSR") == pytest.approx(1.0 / 3.0)
+    assert ec.pct_vs(ms, NAMES, "ELL") == 0.0  # infeasible
+
+
+def _table(n=60):
+    """Feature 3 (min row length) decides: below 10 plain SELL is fastest (1 ms) and
+    SELL the best of the five (2 ms); otherwise CSR (1 ms), everything else 3 ms."""
+    recs = []
+    for i in range(n):
+        small = i % 3 == 0
+        f = [1000.0 + i, 1000.0, 1e-3, 2.0 if small else 20.0, 50.0, 8.0] + [1.0] * 10
+        if small:
+            ms = {"CSR": 3.0, "CSR5": 3.0, "ELL": 3.0, "SELL": 2.0, "HYB": 3.0, "SELL_plain": 1.0, "COO": 3.0}
+        else:
+            ms = {"CSR": 1.0, "CSR5": 3.0, "ELL": 3.0, "SELL": 3.0, "HYB": 3.0, "SELL_plain": 3.0, "COO": 3.0}
+        recs.append({"index": i, "classes": NAMES, "features": f, "ms": ms, "ms_batch": ms})
+    return recs
+
+
+def test_evaluate_closed_forms():
+    recs = _table()
+    r = ec.evaluate(recs, "ms")
+    frac = np.mean([i % 3 == 0 for i in range(60)])
+    assert r["best_counts"]["SELL_plain"] == 20 and r["best_counts"]["CSR"] == 40
+    assert r["extra_best_fraction"] == pytest.approx(frac)
+    # best of seven is 2x faster on the small-row matrices, equal elsewhere
+    assert r["oracle_speedup_of_best7_over_best5"]["mean"] == pytest.approx(2 * frac + (1 - frac))
+    assert r["oracle_speedup_of_best7_over_best5"]["max"] == pytest.approx(2.0)
+    assert r["best5_pct_of_best7_mean"] == pytest.approx(100 * (0.5 * frac + (1 - frac)))
+    # a separable feature: the seven-class tree is exact, the five-class one reaches the five-class optimum
+    _, te = split(60, n_train=48)
+    small_te = np.mean([i % 3 == 0 for i in te])
+    assert r["seven_classes"]["DTC (the paper's)"]["mean_pct_of_best7"] == pytest.approx(100.0)
+    assert r["five_classes"]["DTC (the paper's)"]["mean_pct_of_best7"] == pytest.approx(
+        100 * (0.5 * small_te + (1 - small_te)))
+    assert r["held_out_best5_pct_of_best7"] == pytest.approx(100 * (0.5 * small_te + (1 - small_te)))
