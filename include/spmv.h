@@ -140,11 +140,16 @@ SPMV_API int spmv_convert(spmv_fmt fmt, const spmv_csr* csr, const spmv_params* 
                  spmv_handle** out);
 
 /* y = A x (Sec. II-A), y overwritten (beta = 0).  x holds N doubles and y M
- * doubles, both device memory.  Asynchronous on `stream`; no host sync.
- * Launches the format's kernels: one (CSR, CSR5, ELL, SELL), two (HYB with a
- * COO tail), or one per column panel (SELL in panels, in panel order).  Runs of one handle must not overlap on the GPU
- * (they share the handle's small scratch for rows split across warps); runs
- * of different handles may. */
+ * doubles, both device memory.  Asynchronous on `stream`; no host sync, no
+ * allocation (the call can be captured into a CUDA graph).  Launches the
+ * format's kernels: one (CSR, CSR5, ELL, SELL), two (HYB with a COO tail),
+ * or one per column panel (SELL in panels, in panel order).  They are
+ * launched with programmatic stream serialization: their blocks may become
+ * resident while the kernel ahead of them in `stream` finishes, and each
+ * waits for that kernel to complete (its writes visible) before it touches
+ * memory, so stream order holds as for an ordinary launch.  Runs of one
+ * handle must not overlap on the GPU (they share the handle's small scratch
+ * for rows split across warps); runs of different handles may. */
 SPMV_API int spmv_run(const spmv_handle* h, const double* x, double* y, cudaStream_t stream);
 
 /* Write A back as CSR (ptr[M+1], idx[nnz], val[nnz], device, caller-owned).
