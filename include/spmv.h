@@ -180,7 +180,9 @@ SPMV_API void spmv_free(spmv_handle* h);
  * >= 32, 15 SELL-32 fill; the statistics are over rows floor(k*M/8192),
  * k < 8192, when M > 8192 (all rows otherwise), so the cost does not grow
  * with M.  csr->idx holds csr->nnz entries and needs no particular alignment.
- * One kernel launch (a thread-block cluster), asynchronous. */
+ * The CSR must be well formed (ptr[0] = 0, non-decreasing, ptr[M] = nnz, as
+ * spmv_convert checks); this call does not check it.  One kernel launch (a
+ * thread-block cluster), asynchronous. */
 SPMV_API int spmv_features(const spmv_csr* csr, float* feat_dev, cudaStream_t stream);
 
 /* A trained selector: network parameters (SPMV_MLP_PARAMS floats, W1, b1, W2,

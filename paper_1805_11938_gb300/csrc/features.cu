@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kSample / CTAS)
     {  // one shared atomic per distinct bin in the warp
         const unsigned act = __ballot_sync(dev::kFull, on);
         if (on) {
-            const int bin = len < kLenCap ? len : kLenCap;
+            const int bin = len < 0 ? 0 : (len < kLenCap ? len : kLenCap);  // in range even for a malformed ptr
             const unsigned peers = __match_any_sync(act, bin);
             if (lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (unsigned)__popc(peers));
         }
