@@ -134,8 +134,9 @@ SPMV_API const char* spmv_last_error(void);
  * 0 <= idx < N); a violation returns SPMV_ERR_INVALID_ARG.  params may be
  * NULL (all automatic).  Synchronises `stream` (it reads sizes back).
  * The handle owns copies of everything it needs; free it with spmv_free.
- * Errors: INVALID_ARG, INDEX_OVERFLOW (padded slots >= 2^31 where an int32
- * offset is needed), TOO_LARGE (footprint > max_bytes), ALLOC, CUDA. */
+ * Errors: INVALID_ARG, INDEX_OVERFLOW (nnz >= 2^31: the row pointers are
+ * int32; checked on the host before the CSR is read; padded layouts use 64-bit
+ * offsets), TOO_LARGE (footprint > max_bytes), ALLOC, CUDA. */
 SPMV_API int spmv_convert(spmv_fmt fmt, const spmv_csr* csr, const spmv_params* params, cudaStream_t stream,
                  spmv_handle** out);
 

@@ -268,6 +268,21 @@ def test_too_large_and_alloc_failure():
     assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)  # nothing leaked
 
 
+def test_nnz_beyond_int32_refused():
+    """nnz >= 2^31 does not fit the int32 row pointers: INDEX_OVERFLOW in every
+    format, decided on the host before any of the CSR is read (the buffers
+    behind this descriptor are a small valid matrix)."""
+    a = synth.config1()
+    d = sp.DeviceCSR.from_host(a)
+    d._c = sp._abi.spmv_csr(a.m, a.n, 2**31, d.ptr.data_ptr(), d.idx.data_ptr(), d.val.data_ptr())
+    for fmt in range(5):
+        with pytest.raises(sp.SpmvError) as ei:
+            sp.spmv_convert(fmt, d)
+        assert ei.value.name == "INDEX_OVERFLOW", sp.FORMATS[fmt]
+    d._c = sp._abi.spmv_csr(a.m, a.n, a.nnz, d.ptr.data_ptr(), d.idx.data_ptr(), d.val.data_ptr())
+    sp.spmv_convert(0, d)  # the same buffers with their true nnz convert
+
+
 def test_bad_arguments():
     a = synth.config1()
     d = sp.DeviceCSR.from_host(a)
