@@ -49,3 +49,18 @@ def test_evaluate_closed_forms():
     assert r["five_classes"]["DTC (the paper's)"]["mean_pct_of_best7"] == pytest.approx(
         100 * (0.5 * small_te + (1 - small_te)))
     assert r["held_out_best5_pct_of_best7"] == pytest.approx(100 * (0.5 * small_te + (1 - small_te)))
+
+
+def test_profiler_class_lists():
+    """The five classes are the library's formats in id order (the labels of the shipped
+    tables); the two extra ones are settings of existing kernels."""
+    from paper_1805_11938_gb300 import FORMATS, SPMV_HYB_K_NONE, profile_corpus as pc
+
+    assert [c[0] for c in pc.CLASSES_5] == list(FORMATS)
+    assert [c[1] for c in pc.CLASSES_5] == list(range(5))
+    assert all(c[2] == {} for c in pc.CLASSES_5)
+    extra = {c[0]: c for c in pc.CLASSES_7[5:]}
+    assert pc.CLASSES_7[:5] == pc.CLASSES_5
+    assert extra["SELL_plain"][1] == 3 and extra["SELL_plain"][2] == {"sell_sigma": 1}
+    assert extra["COO"][1] == 4 and extra["COO"][2] == {"hyb_k": SPMV_HYB_K_NONE}
+    assert [c[0] for c in pc.CLASSES_7] == NAMES
