@@ -107,13 +107,14 @@ def launches_per_run(fmt: int, info: dict) -> int:
 def batch_families(infos) -> set:
     """Task families of a batch (include/spmv.h, spmv_batch_build): one
     persistent kernel per family present runs in each replay.  CSR5, ELL, the
-    ELL part of HYB and CSR without nonzeros share one family; SELL has one
-    per chunk size C = 32, 64, 128; CSR tiles and HYB tails have their own."""
+    ELL part of HYB, CSR on the lanes-per-row path and CSR without nonzeros
+    share one family; SELL has one per chunk size C = 32, 64, 128; CSR tiles
+    and HYB tails have their own."""
     families = set()
     for i in infos:
         f, aux = i["fmt"], i["aux"]
         if f == 0:
-            families.add("csr" if aux[0] > 0 else "other")
+            families.add("csr" if aux[0] > 0 and aux[1] == 0 else "other")
         elif f == 3:
             if aux[1] > 0:
                 families.add({32: "sell32", 64: "sell64"}.get(i["params"]["sell_C"], "sell128"))
@@ -285,6 +286,8 @@ def tuning_grid(fmt: int) -> list:
     if fmt == 3:
         return [{"sell_C": 32, "sell_sigma": 1024}, {"sell_C": 32, "sell_sigma": -1}, {"sell_C": 64, "sell_sigma": -1},
                 {"sell_C": 128, "sell_sigma": -1}]
+    if fmt == 0:  # the automatic path choice and the tiles
+        return [{}, {"csr_block_nnz": 352}]
     return [{}]
 
 

@@ -85,7 +85,10 @@ typedef struct {
                               or -1 for the whole matrix (0 -> the whole matrix) */
     int32_t csr5_omega;    /* CSR5 tile width: 32, the warp width, is the only value (0 -> 32) */
     int32_t csr5_sigma;    /* CSR5 tile height, 1..32 (0 -> 32) */
-    int32_t csr_block_nnz; /* CSR nonzeros per warp tile: 0 or 352, the only value (0 -> 352) */
+    int32_t csr_block_nnz; /* CSR product: 352 = warp tiles of 352 nonzeros (any mix of row lengths);
+                              -V (V = 2, 4, 8, 16, 32) = V lanes per row (rows of similar length);
+                              0 = automatic: V lanes when the longest row is at most twice the mean
+                              plus 8, V the smallest power of two >= mean / 8 in [2, 16], else tiles */
     int32_t hyb_k;         /* HYB ELL width: > 0 explicit, 0 -> the typical-length rule,
                               SPMV_HYB_K_NONE -> every entry in the COO part */
     int32_t sell_panel_cols; /* SELL column panels (not in the paper): columns per panel.  The matrix
@@ -234,11 +237,13 @@ SPMV_API int spmv_mlp_forward(const float* theta_dev, const float* X_dev, int32_
 /* ------------------------------------------------------------- batching */
 
 /* Many independent products y_b = A_b x_b in one CUDA graph of persistent
- * launches, one per task family present: CSR5, ELL, the ELL part of HYB and
- * CSR without nonzeros; SELL with C = 32; with C = 64; with C = 128; CSR
- * tiles; HYB tails.  build lays out the work lists over all handles (each
- * keeps its own format) and captures the launches on a stream of its own; the
- * handles must outlive the batch.  A SELL handle in column panels is refused
+ * launches, one per task family present: CSR5, ELL, the ELL part of HYB, CSR
+ * on the lanes-per-row path and CSR without nonzeros; SELL with C = 32; with
+ * C = 64; with C = 128; CSR tiles; HYB tails.  Every matrix's y equals its own
+ * spmv_run bit for bit (the same arithmetic in the same order).  build lays
+ * out the work lists over all handles (each keeps its own format) and
+ * captures the launches on a stream of its own; the handles must outlive the
+ * batch.  A SELL handle in column panels is refused
  * (INVALID_ARG): its panels must run one after another.  Synchronises. */
 SPMV_API int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t stream, spmv_batch** out);
 

@@ -32,11 +32,13 @@ enum TaskKind : int32_t {
     T_SELL = 4,      // 8 SELL units (warp each)
     T_CSR5_ZERO = 5, // 256 empty rows of a CSR5 matrix without nonzeros
     T_HYB_TAIL = 6,  // 8 HYB tail tiles, adding into y
-    T_CSR_ZERO = 7   // 256 rows of a CSR matrix without nonzeros
+    T_CSR_ZERO = 7,  // 256 rows of a CSR matrix without nonzeros
+    T_CSR_LANES = 8  // 256 / V rows of a CSR matrix on the lanes-per-row path
 };
 
 struct MatDesc {
     int32_t fmt, sell_r;
+    int32_t csr_lanes;  // CSR: V lanes per row, 0 for the tiles
     int32_t ell_nb;
     const int32_t* long_rows;
     dev::CsrArgs csr;   // CSR, or the HYB tail (ADD)
@@ -109,6 +111,18 @@ __global__ void __launch_bounds__(256, FAM == F_SELL1 ? 8 : (FAM == F_SELL2 ? 5 
                         a.x = x;
                         a.y = y;
                         dev::csr_zero(a, (int64_t)t.z * 256 + threadIdx.x);
+                        break;
+                    }
+                    case T_CSR_LANES: {  // the same arithmetic as the standalone lanes kernel
+                        const dev::CsrArgs& c = md.csr;
+                        const int64_t row0 = (int64_t)t.z * (256 / md.csr_lanes);
+                        switch (md.csr_lanes) {
+                            case 2: dev::csr_lanes_row<2>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 2, threadIdx.x & 1); break;
+                            case 4: dev::csr_lanes_row<4>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 4, threadIdx.x & 3); break;
+                            case 8: dev::csr_lanes_row<8>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 8, threadIdx.x & 7); break;
+                            case 16: dev::csr_lanes_row<16>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 16, threadIdx.x & 15); break;
+                            default: dev::csr_lanes_row<32>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 32, threadIdx.x & 31); break;
+                        }
                         break;
                     }
                     case T_CSR5: {
@@ -192,6 +206,12 @@ static void fill_desc(const spmv_handle* h, MatDesc& d, std::vector<int4>* L, in
     switch (h->fmt) {
         case SPMV_CSR:
             d.csr = csr_tile_args(h->cu, h->ptr, h->idx, h->val, nullptr, nullptr, nullptr);
+            d.csr_lanes = h->csr_lanes;
+            if (h->csr_lanes > 0) {  // the handle's own path, so the batch gives the same bits
+                for (int64_t g = 0; g < ceil_div(h->m, 256 / h->csr_lanes); ++g)
+                    t1.push_back(make_int4(b, T_CSR_LANES, (int32_t)g, 0));
+                break;
+            }
             for (int64_t g = 0; g < ceil_div(h->cu.n, 8); ++g) tc.push_back(make_int4(b, T_CSR, (int32_t)g, 0));
             if (h->cu.n == 0)
                 for (int64_t g = 0; g < ceil_div(h->m, 256); ++g) t1.push_back(make_int4(b, T_CSR_ZERO, (int32_t)g, 0));

@@ -101,6 +101,7 @@ struct spmv_handle {
     int32_t* idx = nullptr;
     double* val = nullptr;
     spmv::CsrTiles cu;
+    int32_t csr_lanes = 0;  // CSR product: 0 = warp tiles, V = V lanes per row
 
     // CSR5
     int32_t csr5_sigma = 0;

@@ -126,6 +126,25 @@ __device__ __forceinline__ void csr_put(const CsrArgs& a, int32_t r, double s) {
     }
 }
 
+// Rows of similar length: row r by V lanes (lane = this thread's place among
+// them).  Each lane keeps a strided share of the row's entries, the row's
+// lanes reading consecutive addresses together, and a shuffle tree over the
+// V lanes closes the row.  Every thread of the warp must call this (rows past
+// the end contribute nothing).
+template <int V>
+__device__ __forceinline__ void csr_lanes_row(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                              const double* __restrict__ val, const double* __restrict__ x,
+                                              double* __restrict__ y, int32_t m, int64_t r, int lane) {
+    double s = 0.0;
+    if (r < m) {
+        const int32_t p1 = ptr[r + 1];
+        for (int32_t k = ptr[r] + lane; k < p1; k += V) s = fma(__ldcs(val + k), ldx(x, __ldcs(idx + k)), s);
+    }
+#pragma unroll
+    for (int o = V / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o, V);
+    if (r < m && lane == 0) y[r] = s;
+}
+
 // Tile t's part v of row r (tail: r begins in t; else r began earlier).
 template <bool ADD>
 __device__ __forceinline__ void csr_join(const CsrArgs& a, int32_t r, int32_t t, bool tail, double v) {

@@ -13,6 +13,8 @@ def test_batch_families_follow_the_library_grouping():
     assert bench.batch_families([sell32, sell64, sell128]) == {"sell32", "sell64", "sell128"}
     # CSR with tiles, and CSR without nonzeros (zeroed with the plain formats)
     assert bench.batch_families([_info(0, [4, 0, 0, 0]), _info(0, [0, 0, 0, 0])]) == {"csr", "other"}
+    # CSR on the lanes-per-row path (aux[1] = V) runs with the plain formats
+    assert bench.batch_families([_info(0, [4, 4, 0, 0])]) == {"other"}
     # HYB: the ELL part with the plain formats, the tail in its own family only when it has rows
     assert bench.batch_families([_info(4, [2, 7, 3, 1]), _info(4, [2, 0, 3, 0])]) == {"other", "hyb_tail"}
     assert bench.batch_families([_info(4, [2, 0, 3, 0])]) == {"other"}

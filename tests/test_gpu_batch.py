@@ -28,7 +28,8 @@ def _mats(n):
     return out
 
 
-@pytest.mark.parametrize("params", [None, {"csr5_sigma": 4, "sell_C": 128, "sell_sigma": 256, "hyb_k": 2}])
+@pytest.mark.parametrize("params", [None, {"csr5_sigma": 4, "sell_C": 128, "sell_sigma": 256, "hyb_k": 2},
+                                    {"csr_block_nnz": -8}, {"csr_block_nnz": 352}])
 def test_batch_matches_single_runs(sp, params):
     mats = _mats(23)
     handles, xs, ys, ys2, singles = [], [], [], [], []

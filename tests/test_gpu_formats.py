@@ -31,7 +31,7 @@ def _lib():
 
 MATS = matrices_small()
 PARAMS = {
-    0: [None, {"csr_block_nnz": 352}],
+    0: [None, {"csr_block_nnz": 352}, {"csr_block_nnz": -2}, {"csr_block_nnz": -32}],
     1: [None, {"csr5_sigma": 1}, {"csr5_sigma": 4}, {"csr5_sigma": 32}],
     2: [None],
     3: [None, {"sell_C": 64, "sell_sigma": 1}, {"sell_C": 128, "sell_sigma": -1}, {"sell_C": 32, "sell_sigma": 256},
@@ -296,6 +296,8 @@ def test_bad_arguments():
         sp.spmv_convert(sp.SPMV_CSR5, d, {"csr5_omega": 16})
     with pytest.raises(sp.SpmvError):
         sp.spmv_convert(sp.SPMV_CSR, d, {"csr_block_nnz": 1000})
+    with pytest.raises(sp.SpmvError):
+        sp.spmv_convert(sp.SPMV_CSR, d, {"csr_block_nnz": -3})
 
 
 # --------------------------------------------------------------- full size

@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 PARAMS = {
-    0: [None],
+    0: [None, {"csr_block_nnz": 352}, {"csr_block_nnz": -4}, {"csr_block_nnz": -16}],
     1: [None, {"csr5_sigma": 3}, {"csr5_sigma": 17}],
     2: [None],
     3: [None, {"sell_C": 64, "sell_sigma": 128}, {"sell_C": 128, "sell_sigma": 1}, {"sell_panel_cols": 97},
