@@ -64,3 +64,19 @@ def test_profiler_class_lists():
     assert extra["SELL_plain"][1] == 3 and extra["SELL_plain"][2] == {"sell_sigma": 1}
     assert extra["COO"][1] == 4 and extra["COO"][2] == {"hyb_k": SPMV_HYB_K_NONE}
     assert [c[0] for c in pc.CLASSES_7] == NAMES
+
+
+def test_committed_results_reproduce():
+    """data/selector_seven_classes.json is what extra_classes computes from the committed
+    seven-class table."""
+    import json
+    import os
+
+    from paper_1805_11938_gb300.train_selector import load_table
+
+    data = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1805_11938_gb300", "data")
+    recs = load_table(os.path.join(data, "corpus_table7.jsonl"))
+    with open(os.path.join(data, "selector_seven_classes.json")) as f:
+        stored = json.load(f)
+    got = json.loads(json.dumps({key: ec.evaluate(recs, key) for key in ("ms", "ms_batch")}))
+    assert got == stored
