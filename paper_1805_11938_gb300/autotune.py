@@ -8,7 +8,7 @@ Training Data"): repeat until the 95% confidence interval of the mean is
 narrower than 5% of the mean, within a minimum and a maximum count.
 
 tune() searches each format's parameters (SELL C and sigma, CSR5 sigma,
-CSR block budget, HYB K) and keeps the fastest; profile() gives the best time
+the CSR path, HYB K) and keeps the fastest; profile() gives the best time
 of every format, the label used to train the selector.
 """
 from __future__ import annotations
@@ -72,8 +72,8 @@ class Timer:
 
 
 def default_grid(fmt: int, m: int) -> list:
-    if fmt == SPMV_CSR:
-        return [{}]
+    if fmt == SPMV_CSR:  # the automatic path choice, the tiles
+        return [{}, {"csr_block_nnz": 352}]
     if fmt == SPMV_CSR5:
         return [{"csr5_sigma": s} for s in (8, 12, 16, 24, 32)]
     if fmt == SPMV_ELL:
