@@ -31,3 +31,21 @@ def test_launches_per_run():
     assert bench.launches_per_run(3, _info(3, [5, 10, 3, 3], 32)) == 3  # one per column panel
     assert bench.launches_per_run(4, _info(4, [2, 7, 3, 1])) == 2  # ELL part + tail
     assert bench.launches_per_run(4, _info(4, [2, 0, 3, 0])) == 1
+
+
+def test_algorithmic_bytes_closed_forms():
+    """Every stored nonzero once (12 B), x (8N) and y (8M) once, plus each format's
+    metadata, never the padding."""
+    m, n, nnz = 1000, 700, 5000
+    base = 12 * nnz + 8 * n + 8 * m
+
+    def info(aux):
+        return {"m": m, "n": n, "nnz": nnz, "aux": list(aux), "params": {"sell_C": 32}}
+
+    assert bench.algorithmic_bytes(0, info([15, 0, 0, 0])) == base + 4 * (m + 1)     # CSR: ptr
+    assert bench.algorithmic_bytes(1, info([5, 0, 0, 0])) == base + 5 * 160          # CSR5: 160 B per tile
+    assert bench.algorithmic_bytes(2, info([7, 0, 0, 0])) == base + 4 * m            # ELL: row_len
+    assert bench.algorithmic_bytes(3, info([32, 40, 9, 0])) == base + 8 * m + 8 * 33 + 8 * 40  # SELL
+    assert bench.algorithmic_bytes(4, info([2, 30, 3, 1])) == base + 4 * m + 16 * 30  # HYB: 16 B per tail row
+    # the padding a layout stores does not count: the same matrix in ELL moves the same nonzeros
+    assert bench.algorithmic_bytes(2, info([7000, 0, 0, 0])) == bench.algorithmic_bytes(2, info([7, 0, 0, 0]))
