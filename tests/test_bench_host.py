@@ -49,3 +49,20 @@ def test_algorithmic_bytes_closed_forms():
     assert bench.algorithmic_bytes(4, info([2, 30, 3, 1])) == base + 4 * m + 16 * 30  # HYB: 16 B per tail row
     # the padding a layout stores does not count: the same matrix in ELL moves the same nonzeros
     assert bench.algorithmic_bytes(2, info([7000, 0, 0, 0])) == bench.algorithmic_bytes(2, info([7, 0, 0, 0]))
+
+
+def test_clock_sampler_summary():
+    """nvidia-smi lines (no GPU needed): median SM clock, maximum clock, and the throttle
+    reasons seen active in any sample; malformed lines are skipped."""
+    cs = bench.ClockSampler(0)
+    cs.f.write("0, 2070, 2070, 812.3, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+               "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+               "garbage line\n"
+               "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s = cs.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    cs2 = bench.ClockSampler(0)
+    cs2.f.write("0, 1000, 2070, 500, 0x8, Active, Not Active, Active, Not Active\n")
+    assert cs2.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+    assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
+                                               "samples": 0}
