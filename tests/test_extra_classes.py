@@ -80,3 +80,33 @@ def test_committed_results_reproduce():
         stored = json.load(f)
     got = json.loads(json.dumps({key: ec.evaluate(recs, key) for key in ("ms", "ms_batch")}))
     assert got == stored
+
+
+def test_replica_is_block_diagonal():
+    """The throughput label's matrix diag(A, ..., A): k copies of A's rows, columns
+    shifted by the copy, values repeated; its product is k copies of A x."""
+    import synth
+    import oracle
+    from paper_1805_11938_gb300 import profile_corpus as pc
+
+    a = synth.tiny_random(7, 5, 0.5, 21)
+    r = pc.replica(a, 3)
+    assert (r.m, r.n, int(r.ptr[-1])) == (3 * a.m, 3 * a.n, 3 * a.nnz)
+    x = synth.vector(r.n, 4)
+    y = oracle.csr_spmv(r, x)
+    for c in range(3):
+        assert np.array_equal(y[c * a.m:(c + 1) * a.m], oracle.csr_spmv(a, x[c * a.n:(c + 1) * a.n]))
+    assert pc.replica(a, 1) is a
+
+
+def test_replica_count_rule():
+    """About 2^23 nonzeros in the replica, one copy for large or empty matrices, indices within int32."""
+    import synth
+    from paper_1805_11938_gb300 import profile_corpus as pc
+
+    a = synth.tiny_random(7, 5, 0.5, 21)
+    k = pc.replica_count(a)
+    assert k * a.nnz >= pc.REPLICA_NNZ and (k - 1) * a.nnz < pc.REPLICA_NNZ
+    assert k * max(a.m, a.n) < 2**31
+    empty = synth.from_lengths_random_cols(np.zeros(4, np.int32), 3, 1, "empty")
+    assert pc.replica_count(empty) == 1
