@@ -115,7 +115,7 @@ typedef struct {
     int64_t stored_slots;   /* value slots stored, padding included */
     spmv_params params;     /* resolved tuning parameters (hyb_k: the K used) */
     int64_t aux[4];         /* format detail (see spmv_handle_array for the arrays):
-                               CSR  {warp tiles, 0, 0, 0}
+                               CSR  {warp tiles, lanes per row (0: the tiles run), 0, 0}
                                CSR5 {tiles, tiles listing their rows, empty rows, 0}
                                ELL  {K, rows left to whole blocks, their length threshold, 0}
                                SELL {slices, warp units, longest row, column panels (0: one)}
