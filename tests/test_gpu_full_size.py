@@ -1,8 +1,8 @@
 """Parity at the workloads' full sizes, in the configurations bench.py times,
 on sampled rows the oracle computes one by one.
 
-  * 27-point stencil on 224^3 (300.8 M nonzeros): HYB (the selector's pick),
-    ELL and SELL.
+  * 27-point stencil on 224^3 (300.8 M nonzeros): HYB, ELL and SELL (the
+    selector's pick).
   * 2e7-row power-law graph (239 M nonzeros): SELL in its automatic column
     panels (x is 160 MB) and CSR5.
   * the 512-matrix batch with the formats the batch model picks: every
