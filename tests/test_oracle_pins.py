@@ -228,6 +228,40 @@ def test_within_error_bound_of_exact_sum():
         assert abs(Fraction(float(y[i])) - ex) <= Fraction(float(b[i]))
 
 
+
+def test_fp_bound_hand_computed():
+    """The tolerance 4 * nnz_i * 2^-53 * sum_j |a_ij x_j|, worked by hand row by
+    row as exact multiples of 2^-53 (small integers and powers of two, so every
+    step is exact in FP64).  Rows of different lengths catch a wrong nnz_i
+    factor; signed entries catch a dropped absolute value; the duplicate pair
+    cancels in y but not in the bound."""
+    u = 2.0 ** -53
+    # row 0: {2, -3} on x = (1, 1)             -> 4 * 2 * (2 + 3)       = 40 u
+    # row 1: empty                              -> 0
+    # row 2: {0.5} on x_1 = -4                  -> 4 * 1 * 2             =  8 u
+    # row 3: {-2, 3, 1} on x = (-1, 2, -0.25)   -> 4 * 3 * (2 + 6 + 0.25) = 99 u
+    # row 4: duplicates {1.5, -1.5} in column 0 -> 4 * 2 * (3 + 3)       = 48 u
+    ptr = np.array([0, 2, 2, 3, 6, 8], np.int32)
+    idx = np.array([0, 1, 1, 0, 1, 2, 0, 0], np.int32)
+    val = np.array([2.0, -3.0, 0.5, -2.0, 3.0, 1.0, 1.5, -1.5])
+    a = synth.CSR(5, 3, ptr, idx, val, "bound_rows")
+    x = np.array([1.0, 1.0, 1.0])
+    assert oracle.fp_bound(a, x)[[0, 1]].tolist() == [40 * u, 0.0]
+    x = np.array([-1.0, -4.0, -0.25])
+    b = oracle.fp_bound(a, x)
+    assert b[1] == 0.0 and b[2] == 4 * 1 * 2.0 * u
+    x = np.array([-1.0, 2.0, -0.25])
+    b = oracle.fp_bound(a, x)
+    assert b[3] == 4 * 3 * 8.25 * u
+    x = np.array([2.0, 0.0, 0.0])
+    b = oracle.fp_bound(a, x)
+    assert b[4] == 48 * u and oracle.csr_spmv(a, x)[4] == 0.0
+    assert b[0] == 4 * 2 * 4.0 * u  # |2 * 2| + |-3 * 0|
+    # the bound scales with |x| and is zero exactly on rows whose products all vanish
+    assert np.array_equal(oracle.fp_bound(a, 2.0 * x), 2.0 * b)
+    assert oracle.fp_bound(a, np.zeros(3)).tolist() == [0.0] * 5
+
+
 # ------------------------------------------------------- converters, brute force
 
 def _patterns():
@@ -466,6 +500,37 @@ def test_adam_first_step_is_signed_lr():
     assert np.allclose(th[:3], [-0.01, 0.01, -0.01], rtol=1e-9)
     assert th[3] == 0.0
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+
+
+
+def test_adam_constant_gradient_moves_lr_every_step():
+    """With a constant gradient g, Adam's bias-corrected moments are exactly g
+    and g^2 at every step t (m_t = (1 - beta1^t) g, v_t = (1 - beta2^t) g^2),
+    so each step moves every parameter by lr against the sign of g.  A wrong
+    step number in the bias correction breaks this from t = 2 on (with t = 1
+    throughout, step 2 would move by lr * 1.9 / sqrt(1.999))."""
+    g = np.array([3.0, -2.0, 1e-3, 0.5])
+    th, m, v = np.zeros(4), np.zeros(4), np.zeros(4)
+    for t in range(1, 6):
+        prev = th
+        th, m, v = mlp.adam_step(th, g, m, v, t, lr=0.01, eps=0.0)
+        assert np.allclose(prev - th, 0.01 * np.sign(g), rtol=1e-9, atol=0), t
+
+
+def test_adam_steps_two_and_three_hand_worked():
+    """Gradient 1 at step 1, then 0 at steps 2 and 3 (beta1 0.9, beta2 0.999,
+    lr 0.01).  By hand: m_2 = 0.09, v_2 = 0.000999, so the step-2 move is
+    0.01 * (0.09 / 0.19) / sqrt(0.000999 / 0.001999) = 0.01 * (9/19) /
+    sqrt(999/1999); m_3 = 0.081, v_3 = 0.000998001, and the step-3 move is
+    0.01 * (81/271) / sqrt(998001/2997001)."""
+    th, m, v = mlp.adam_step(np.zeros(1), np.ones(1), np.zeros(1), np.zeros(1), 1, lr=0.01, eps=0.0)
+    assert th[0] == pytest.approx(-0.01, rel=1e-12)
+    th2, m, v = mlp.adam_step(th, np.zeros(1), m, v, 2, lr=0.01, eps=0.0)
+    assert m[0] == pytest.approx(0.09, rel=1e-14) and v[0] == pytest.approx(0.000999, rel=1e-14)
+    assert th[0] - th2[0] == pytest.approx(0.01 * (9 / 19) / math.sqrt(999 / 1999), rel=1e-12)
+    th3, m, v = mlp.adam_step(th2, np.zeros(1), m, v, 3, lr=0.01, eps=0.0)
+    assert m[0] == pytest.approx(0.081, rel=1e-14) and v[0] == pytest.approx(0.000998001, rel=1e-14)
+    assert th2[0] - th3[0] == pytest.approx(0.01 * (81 / 271) / math.sqrt(998001 / 2997001), rel=1e-12)
 
 
 def test_scaling_min_max():
