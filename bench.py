@@ -535,8 +535,10 @@ def main():
 
     # ---- gather ceiling of this matrix's index stream: val[k] * x[idx[k]] for
     # every entry, one gather and one DFMA each, no row structure
-    probe_part = torch.empty(sp._abi.PROBE_PARTIALS, dtype=torch.float64, device="cuda")
-    probe_ms = statistics.mean(timed(lambda: sp.spmv_probe_gather(d, x, probe_part), args.format_steps, 5))
+    from paper_1805_11938_gb300 import probe
+
+    probe_part = torch.empty(probe.partials(), dtype=torch.float64, device="cuda")
+    probe_ms = statistics.mean(timed(lambda: probe.gather(d, x, probe_part), args.format_steps, 5))
     # ---- the selected format's parameters from the autotuner's grid (one-off
     # setup, like the conversion): the fastest of the default and the grid
     hc = handles[chosen]

@@ -263,10 +263,13 @@ SPMV_API void spmv_batch_free(spmv_batch* b);
 
 /* y = A x straight from a caller's device CSR (no handle), allocating no
  * device memory at all.  For callers that cannot call cudaMalloc when they
- * need the product: code running while a stream is captured into a CUDA
- * graph, code under an allocator that owns every device byte, or paths that
- * must not enter the allocator.  The paper has no counterpart: it is an
- * interface of this library, computing the same y as spmv_run.
+ * need the product: code running under a memory manager that has already
+ * reserved every device byte (a framework's caching allocator, an
+ * application's own pool), and latency-critical paths that must not enter
+ * the CUDA allocator, whose calls can synchronise the whole device.  The
+ * paper has no counterpart: it is an interface of this library, computing
+ * the same y as spmv_run on a CSR handle (within the FP64 tolerance; bit for
+ * bit on integer-valued inputs).
  *  - csr, x, y: device arrays owned by the caller, layout as for spmv_convert;
  *    the CSR is not validated (pass one that spmv_convert accepts).
  *  - Scratch: a static device array of this library (6 MiB, held by every
@@ -278,23 +281,6 @@ SPMV_API void spmv_batch_free(spmv_batch* b);
  *    whose kernels overlap on the GPU (different streams, no ordering) race.
  *  - Asynchronous on `stream`; two kernel launches. */
 SPMV_API int spmv_csr_run_noalloc(const spmv_csr* csr, const double* x, double* y, cudaStream_t stream);
-
-/* ------------------------------------------------------------ measurement */
-
-/* The gather ceiling of a product on a given index stream: sums
- * val[k] * x[idx[k]] over k < nnz with one random gather and one DFMA per
- * entry and no row structure (a grid-stride stream over the arrays with
- * coalesced loads of idx and val and the gathers through the read-only path,
- * as the product kernels issue them).  Not in the paper: a measurement aid;
- * its time on a matrix's own idx/val is the practical roofline of an SpMV on
- * that matrix when the gathers, not HBM, bound it.
- *  - idx, val: nnz entries, x: indexed by idx; all device memory.
- *  - partial: SPMV_PROBE_PARTIALS doubles of device memory, overwritten with
- *    one partial sum per thread (their sum is the total).
- *  - Asynchronous on `stream`; one launch. */
-#define SPMV_PROBE_PARTIALS (152 * 8 * 256)
-SPMV_API int spmv_probe_gather(const int32_t* idx, const double* val, int64_t nnz, const double* x, double* partial,
-                               cudaStream_t stream);
 
 /* --------------------------------------------------------- fault testing */
 

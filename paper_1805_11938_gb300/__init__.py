@@ -26,7 +26,7 @@ __all__ = [
     "SpmvError", "DeviceCSR", "Handle", "Model", "Batch", "spmv_convert", "spmv_run", "spmv_to_csr",
     "spmv_features", "spmv_select", "spmv_select_async", "spmv_mlp_scale", "spmv_mlp_loss_grad", "spmv_mlp_adam",
     "spmv_mlp_train", "spmv_mlp_forward", "spmv_batch_build", "spmv_batch_run", "spmv_batch_run_separate",
-    "spmv_csr_run_noalloc", "spmv_debug_fail_alloc", "spmv_debug_features_cluster", "spmv_probe_gather", "lib",
+    "spmv_csr_run_noalloc", "spmv_debug_fail_alloc", "spmv_debug_features_cluster", "lib",
 ]
 
 
@@ -327,17 +327,6 @@ def spmv_debug_fail_alloc(k: int) -> None:
 
 def spmv_debug_features_cluster(ctas: int) -> None:
     lib().spmv_debug_features_cluster(int(ctas))
-
-
-def spmv_probe_gather(csr: DeviceCSR, x, partial=None, stream=None):
-    """Partial sums of val[k] * x[idx[k]] over the CSR's entries: the gather
-    ceiling of a product on this index stream (a measurement aid)."""
-    torch = _torch()
-    if partial is None:
-        partial = torch.empty(_abi.PROBE_PARTIALS, dtype=torch.float64, device=x.device)
-    check(lib().spmv_probe_gather(_vp(csr.idx), _vp(csr.val), int(csr.nnz), _vp(x), _vp(partial), _stream(stream)),
-          "spmv_probe_gather")
-    return partial
 
 
 # the selector trained on single-product times (spmv_select's default use), and

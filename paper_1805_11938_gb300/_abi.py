@@ -82,9 +82,7 @@ _SIGS = {
     "spmv_csr_run_noalloc": (ctypes.c_int, [ctypes.POINTER(spmv_csr), _VP, _VP, _VP]),
     "spmv_debug_fail_alloc": (None, [_I32]),
     "spmv_debug_features_cluster": (None, [_I32]),
-    "spmv_probe_gather": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP, _VP, _VP]),
 }
-PROBE_PARTIALS = 152 * 8 * 256
 EXPORTED = tuple(_SIGS)
 
 

@@ -20,6 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspmv_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+PROBE_SRC = os.path.join(HERE, "probe", "gather.cu")
+PROBE_LIB = os.path.join(HERE, "probe", "libspmv_probe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
@@ -42,10 +44,26 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    for lib, deps in ((LIB, _deps()), (PROBE_LIB, [PROBE_SRC])):
+        if not os.path.exists(lib):
+            return False
+        t = os.path.getmtime(lib)
+        if any(os.path.getmtime(d) > t for d in deps):
+            return False
+    return True
+
+
+def build_probe(cc: str) -> str:
+    """The benchmark's gather-ceiling probe, a shared library of its own (not
+    part of the library's ABI)."""
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    cmd = [cc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+           "-shared", "-cudart", "static", "-o", tmp, PROBE_SRC]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on the probe:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -65,9 +83,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(r.stdout, r.stderr, file=sys.stderr)
         return obj
 
-    workers = max(1, min(len(srcs), os.cpu_count() or 4))
+    workers = max(1, min(len(srcs) + 1, os.cpu_count() or 4))
     with cf.ThreadPoolExecutor(workers) as ex:
+        probe = ex.submit(build_probe, cc)
         objs = list(ex.map(compile_one, srcs))
+        probe.result()
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-Xcompiler", "-fPIC"]
     r = subprocess.run(cmd, capture_output=True, text=True)

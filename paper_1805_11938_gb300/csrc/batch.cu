@@ -16,6 +16,7 @@
 // blocks) 256-thread blocks that take tasks from an atomic counter until the
 // list is exhausted (no block ever waits on another).  run uploads the x/y
 // pointer tables when they change and replays the graph.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -377,14 +378,19 @@ static int upload_vectors(spmv_batch* bt, const double* const* xs, double* const
     bool same = true;
     for (int32_t b = 0; b < bt->count && same; ++b) same = bt->xs[b] == xs[b] && bt->ys[b] == ys[b];
     if (same) return SPMV_OK;
-    for (int32_t b = 0; b < bt->count; ++b) {
+    for (int32_t b = 0; b < bt->count; ++b)
         if (!xs[b] || !ys[b]) return set_error(SPMV_ERR_INVALID_ARG, "x or y of matrix %d is NULL", b);
-        bt->xs[b] = xs[b];
-        bt->ys[b] = ys[b];
-    }
-    SPMV_CUDA(cudaMemcpyAsync(bt->d_xs, bt->xs.data(), sizeof(double*) * bt->count, cudaMemcpyHostToDevice, stream));
-    SPMV_CUDA(cudaMemcpyAsync(bt->d_ys, bt->ys.data(), sizeof(double*) * bt->count, cudaMemcpyHostToDevice, stream));
-    SPMV_CUDA(cudaStreamSynchronize(stream));  // the host tables are reused on the next call
+    // The cached host tables describe what the device tables hold: forget them
+    // until both copies have landed, so a failed upload is retried in full.
+    std::fill(bt->xs.begin(), bt->xs.end(), nullptr);
+    std::fill(bt->ys.begin(), bt->ys.end(), nullptr);
+    std::vector<const double*> hx(xs, xs + bt->count);
+    std::vector<double*> hy(ys, ys + bt->count);
+    SPMV_CUDA(cudaMemcpyAsync(bt->d_xs, hx.data(), sizeof(double*) * bt->count, cudaMemcpyHostToDevice, stream));
+    SPMV_CUDA(cudaMemcpyAsync(bt->d_ys, hy.data(), sizeof(double*) * bt->count, cudaMemcpyHostToDevice, stream));
+    SPMV_CUDA(cudaStreamSynchronize(stream));  // the staging vectors go out of scope
+    bt->xs.assign(hx.begin(), hx.end());
+    bt->ys.assign(hy.begin(), hy.end());
     return SPMV_OK;
 }
 
@@ -402,7 +408,12 @@ int spmv_batch_run_separate(spmv_batch* bt, const double* const* xs, double* con
     if (!same) {
         bt->sep_xs.assign(xs, xs + bt->count);
         bt->sep_ys.assign(ys, ys + bt->count);
-        SPMV_TRY(capture_separate(bt));
+        const int st = capture_separate(bt);
+        if (st != SPMV_OK) {  // no graph for these vectors: the next call captures again
+            bt->sep_xs.clear();
+            bt->sep_ys.clear();
+            return st;
+        }
     }
     SPMV_CUDA(cudaGraphLaunch(bt->exec_sep, stream));
     return SPMV_OK;

@@ -32,6 +32,24 @@ int cuda_error(cudaError_t e, const char* what) {
 
 void debug_fail_alloc(int k) { g_fail_alloc_countdown.store(k); }
 
+int sm_count() {
+    static std::atomic<int> cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    int n = cached[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+            (void)cudaGetLastError();
+            n = 1;
+        }
+        cached[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 int dev_malloc(void** p, size_t bytes) {
     int c = g_fail_alloc_countdown.load();
     while (c > 0) {
@@ -90,8 +108,7 @@ int validate_csr(const spmv_csr* c, cudaStream_t s) {
     SPMV_CUDA(cudaMemsetAsync(err, 0, sizeof(int), s));
     k_validate_ptr<<<grid_for((int64_t)c->m + 1, 256), 256, 0, s>>>(c->ptr, c->m, c->nnz, err);
     if (c->nnz > 0) {
-        int g = grid_for(c->nnz, 256);
-        if (g > 152 * 32) g = 152 * 32;
+        int g = grid_capped(c->nnz, 256, 32);
         k_validate_idx<<<g, 256, 0, s>>>(c->idx, c->nnz, c->n, err);
     }
     SPMV_CUDA(cudaGetLastError());
@@ -235,8 +252,7 @@ int max_i32(const int32_t* a, int64_t n, int32_t* result_host, cudaStream_t s, S
     int32_t* d = nullptr;
     SPMV_TRY(tmp.get(&d, 1));
     SPMV_CUDA(cudaMemsetAsync(d, 0, sizeof(int32_t), s));
-    int g = grid_for(n, 256);
-    if (g > 152 * 16) g = 152 * 16;
+    int g = grid_capped(n, 256, 16);
     if (n > 0) k_max_i32<<<g, 256, 0, s>>>(a, n, d);
     SPMV_CUDA(cudaGetLastError());
     SPMV_CUDA(cudaMemcpyAsync(result_host, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s));

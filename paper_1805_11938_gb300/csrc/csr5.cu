@@ -166,8 +166,7 @@ int csr5_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     if (nt > 0) {
         k_flags<<<grid_for(nt * 32, 256), 256, 0, s>>>(c->ptr, m, c->nnz, nt, sigma, h->flags);
         k_desc<<<grid_for(nt * 32, 256), 256, 0, s>>>(h->flags, nt, h->y_off, h->seg_off, nflag);
-        int g = grid_for(nt * S, 256);
-        if (g > 152 * 64) g = 152 * 64;
+        int g = grid_capped(nt * S, 256, 64);
         k_tiles<<<g, 256, 0, s>>>(c->idx, c->val, c->nnz, nt, sigma, h->tile_idx, h->tile_val);
     }
     // empty rows: flags, prefix counts, and the rows listed per tile
@@ -241,8 +240,7 @@ __global__ void k_untile(const int32_t* __restrict__ tidx, const double* __restr
 int csr5_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, cudaStream_t s) {
     SPMV_CUDA(cudaMemcpyAsync(ptr, h->ptr, sizeof(int32_t) * ((size_t)h->m + 1), cudaMemcpyDeviceToDevice, s));
     if (h->nnz > 0) {
-        int g = grid_for(h->nnz, 256);
-        if (g > 152 * 64) g = 152 * 64;
+        int g = grid_capped(h->nnz, 256, 64);
         k_untile<<<g, 256, 0, s>>>(h->tile_idx, h->tile_val, h->nnz, h->csr5_sigma, idx, val);
     }
     SPMV_CUDA(cudaGetLastError());

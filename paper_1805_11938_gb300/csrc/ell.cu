@@ -61,8 +61,7 @@ int ell_build(spmv_handle* h, EllPart& e, const spmv_csr* c, int32_t K, const in
     }
     k_ell_row_len<<<grid_for(m, 256), 256, 0, s>>>(len, m, K, e.row_len);
     if (c->nnz > 0 && K > 0) {
-        int g = grid_for(c->nnz, 256);
-        if (g > 152 * 64) g = 152 * 64;
+        int g = grid_capped(c->nnz, 256, 64);
         k_ell_scatter<<<g, 256, 0, s>>>(c->ptr, c->idx, c->val, m, c->nnz, K, e.ld, e.col, e.val);
     }
     SPMV_CUDA(cudaGetLastError());
@@ -146,8 +145,7 @@ int ell_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, cu
     Scratch tmp;
     SPMV_TRY(exclusive_scan<int32_t>(h->ell.row_len, ptr, h->m, s, tmp));
     if (h->nnz > 0) {
-        int g = grid_for(h->nnz, 256);
-        if (g > 152 * 64) g = 152 * 64;
+        int g = grid_capped(h->nnz, 256, 64);
         k_ell_gather<<<g, 256, 0, s>>>(ptr, h->m, h->nnz, h->ell.ld, h->ell.col, h->ell.val, idx, val);
     }
     SPMV_CUDA(cudaGetLastError());

@@ -125,8 +125,7 @@ int hyb_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     SPMV_TRY(h->alloc(&h->tail_col, (size_t)nt, "tail_col"));
     SPMV_TRY(h->alloc(&h->tail_val, (size_t)nt, "tail_val"));
     if (nt > 0) {
-        int g = grid_for(c->nnz, 256);
-        if (g > 152 * 64) g = 152 * 64;
+        int g = grid_capped(c->nnz, 256, 64);
         k_tail_scatter<<<g, 256, 0, s>>>(c->ptr, c->idx, c->val, m, c->nnz, K, tpos, h->tail_ptr, h->tail_col,
                                          h->tail_val);
         SPMV_CUDA(cudaGetLastError());
@@ -197,8 +196,7 @@ int hyb_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, cu
     SPMV_CUDA(cudaGetLastError());
     SPMV_TRY(exclusive_scan<int32_t>(len, ptr, h->m, s, tmp));
     if (h->nnz > 0) {
-        int g = grid_for(h->nnz, 256);
-        if (g > 152 * 64) g = 152 * 64;
+        int g = grid_capped(h->nnz, 256, 64);
         k_hyb_gather<<<g, 256, 0, s>>>(ptr, h->m, h->nnz, h->ell.K, h->ell.ld, h->ell.col, h->ell.val, tpos,
                                        h->tail_ptr, h->tail_col, h->tail_val, idx, val);
     }

@@ -217,6 +217,17 @@ inline int grid_for(int64_t n, int per_block) {
     return (int)(g < 1 ? 1 : (g > 0x7fffffff ? 0x7fffffff : g));
 }
 
+// Streaming multiprocessors of the current device (queried once per device).
+int sm_count();
+
+// grid_for, capped at blocks_per_sm blocks per SM of the current device (for
+// grid-stride kernels, whose blocks loop over the rest).
+inline int grid_capped(int64_t n, int per_block, int blocks_per_sm) {
+    const int g = grid_for(n, per_block);
+    const int cap = sm_count() * blocks_per_sm;
+    return g < cap ? g : cap;
+}
+
 // Launch with programmatic stream serialization: the kernel's blocks may get
 // resident while the kernel ahead of it in the stream is still finishing
 // (that kernel lets them in with dev::pdl_trigger(), or simply by ending).

@@ -2,12 +2,12 @@
 // handle and no device allocation of any kind.
 //
 // Who needs it: callers that cannot call cudaMalloc at the moment they need a
-// product -- code running while a stream is being captured into a CUDA graph
-// (allocation calls are not capturable), code that runs under a memory
-// manager which owns every device byte, or latency-critical paths that must
-// not enter the allocator.  They pass inputs and outputs they already own;
-// the little scratch the method needs lives in this file's static device
-// array instead.
+// product -- code that runs under a memory manager which has already reserved
+// every device byte (a framework's caching allocator, an application's own
+// pool), or latency-critical paths that must not enter the CUDA allocator,
+// whose calls can synchronise the whole device.  They pass inputs and outputs
+// they already own; the little scratch the method needs lives in this file's
+// static device array instead.
 //
 // Method: the same segmented-sum scheme as the CSR5 kernels, on the plain CSR
 // order.  The nonzeros are cut into tiles of 32 x kNaSigma; lane c of the warp
@@ -170,8 +170,7 @@ extern "C" SPMV_API int spmv_csr_run_noalloc(const spmv_csr* csr, const double* 
         k_na_tiles<<<grid_for(ntiles * 32, 256), 256, 0, stream>>>(csr->ptr, csr->idx, csr->val, csr->m, csr->nnz,
                                                                    ntiles, x, y, sc);
     const int64_t n2 = ntiles > csr->m ? ntiles : csr->m;
-    int g = grid_for(n2, 256);
-    if (g > 152 * 32) g = 152 * 32;
+    const int g = grid_capped(n2, 256, 32);
     k_na_calibrate<<<g, 256, 0, stream>>>(csr->ptr, csr->m, ntiles, y, sc);
     SPMV_CUDA(cudaGetLastError());
     return SPMV_OK;

@@ -179,8 +179,7 @@ static int sell_build(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
         SPMV_CUDA(cudaMemsetAsync(h->sell_val, 0, sizeof(double) * (size_t)total, s));
     }
     if (c->nnz > 0) {
-        int g = grid_for(c->nnz, 256);
-        if (g > 152 * 64) g = 152 * 64;
+        int g = grid_capped(c->nnz, 256, 64);
         k_sell_scatter<<<g, 256, 0, s>>>(c->ptr, c->idx, c->val, m, c->nnz, ipos, h->slice_ptr, C, h->sell_col,
                                          h->sell_val);
     }
@@ -424,8 +423,7 @@ int sell_to_csr(const spmv_handle* h, int32_t* ptr, int32_t* idx, double* val, c
         SPMV_TRY(tmp.get(&sv, (size_t)c->nnz + 1));
         SPMV_TRY(sell_to_csr_one(c, sp, si, sv, s));
         if (c->nnz > 0) {
-            int g = grid_for(c->nnz, 256);
-            if (g > 152 * 64) g = 152 * 64;
+            int g = grid_capped(c->nnz, 256, 64);
             k_panel_unscatter<<<g, 256, 0, s>>>(si, sv, h->panel_pos[p], c->nnz, (int32_t)(p * h->panel_cols), idx, val);
             SPMV_CUDA(cudaGetLastError());
         }
@@ -443,8 +441,7 @@ static int sell_to_csr_one(const spmv_handle* h, int32_t* ptr, int32_t* idx, dou
     SPMV_CUDA(cudaGetLastError());
     SPMV_TRY(exclusive_scan<int32_t>(len, ptr, h->m, s, tmp));
     if (h->nnz > 0) {
-        int g = grid_for(h->nnz, 256);
-        if (g > 152 * 64) g = 152 * 64;
+        int g = grid_capped(h->nnz, 256, 64);
         k_sell_gather<<<g, 256, 0, s>>>(ptr, h->m, h->nnz, ipos, h->slice_ptr, h->sell_C, h->sell_col, h->sell_val, idx,
                                         val);
     }

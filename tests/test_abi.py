@@ -93,3 +93,18 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[f"{name} size"]) == ctypes.sizeof(cls), name
         for f, _ in cls._fields_:
             assert int(got[f"{name}.{f}"]) == getattr(cls, f).offset, (name, f)
+
+
+def test_probe_is_a_separate_library(lib):
+    """The benchmark's gather probe is not part of the library's ABI: it lives in
+    a shared library of its own, which exports exactly its two calls."""
+    import subprocess
+
+    from paper_1805_11938_gb300 import _abi, build, probe
+
+    assert not hasattr(lib, "spmv_probe_gather")
+    out = subprocess.run(["nm", "-D", "--defined-only", build.PROBE_LIB], capture_output=True, text=True).stdout
+    syms = sorted(l.split()[-1] for l in out.splitlines() if " T " in l and l.split()[-1].startswith("spmv_"))
+    assert syms == ["spmv_probe_gather", "spmv_probe_partials"]
+    assert not any(n.startswith("spmv_probe") for n in _abi.EXPORTED)
+    assert probe.LIB_PATH == build.PROBE_LIB

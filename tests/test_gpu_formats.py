@@ -15,6 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 sp = None
+probe = None
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -23,9 +24,11 @@ def _lib():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_1805_11938_gb300 as m
+    from paper_1805_11938_gb300 import probe as pr
 
     m.lib()
     sp = m
+    globals()["probe"] = pr
     yield
 
 
@@ -331,11 +334,11 @@ def test_full_size_ell_refused_under_cap(cfg2):
 
 
 def test_gather_probe_sums_every_product():
-    """The gather-ceiling probe touches every entry once: with integer values
+    """The benchmark's gather-ceiling probe touches every entry once: with integer values
     its partial sums add up exactly to sum(val[k] * x[idx[k]])."""
     for mi in (1, 9, 10):
         a = synth.with_integer_values(MATS[mi], 31 + mi)
         x = synth.integers(a.n, 32 + mi, -16, 16)
-        part = sp.spmv_probe_gather(sp.DeviceCSR.from_host(a), torch.as_tensor(x).cuda()).cpu().numpy()
+        part = probe.gather(sp.DeviceCSR.from_host(a), torch.as_tensor(x).cuda()).cpu().numpy()
         exact = int(np.sum(a.val.astype(np.int64) * x.astype(np.int64)[a.idx]))
         assert part.sum() == float(exact), (a.name, part.sum(), exact)

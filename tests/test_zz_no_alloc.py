@@ -1,12 +1,14 @@
-"""The allocation-free entry point against the ordinary one.
+"""The allocation-free entry point against the ordinary one and the oracle.
 
 spmv_csr_run_noalloc serves callers that cannot call cudaMalloc when they need
-a product (inside graph capture, under an allocator owning all device memory,
-on allocation-free paths); it keeps its scratch in a static device array of
-the library.  Two calls in a row (the second reusing the array the first left
-behind) must each match spmv_run on a converted handle within the FP64
-tolerance used throughout the tests.  The file name sorts last so a run that
-stops at the first failure has already run every other test.
+a product: code under a memory manager that has already reserved every device
+byte, or latency-critical paths that must not enter the CUDA allocator (its
+calls can synchronise the device).  It keeps its scratch in a static device
+array of the library.  Two calls in a row (the second reusing the array the
+first left behind) must each match spmv_run on a converted handle and the CPU
+oracle within the FP64 tolerance used throughout the tests, and, on
+integer-valued inputs, both bit for bit.  The file name sorts last so a run
+that stops at the first failure has already run every other test.
 """
 import numpy as np
 import pytest
@@ -50,6 +52,25 @@ def test_noalloc_matches_spmv_run_twice(sp, ci):
         y = y.cpu().numpy()
         bound = oracle.fp_bound(a, xh)
         assert np.all(np.abs(y - y_ref) <= bound), (a.name, call, float(np.max(np.abs(y - y_ref) - bound)))
+        y_or = oracle.csr_spmv(a, xh)
+        assert np.all(np.abs(y - y_or) <= bound), (a.name, call, float(np.max(np.abs(y - y_or) - bound)))
+
+
+@pytest.mark.parametrize("ci", range(5))
+def test_noalloc_integer_values_bit_exact_twice(sp, ci):
+    """Small integer values and x: every summation order gives the exact row
+    sums, so y equals the oracle's and spmv_run's bit for bit."""
+    a = synth.with_integer_values(_cases()[ci], 60 + ci)
+    d = sp.DeviceCSR.from_host(a)
+    h = sp.spmv_convert(sp.SPMV_CSR, d)
+    for call in range(2):
+        xh = synth.integers(a.n, 70 + ci + 10 * call, -16, 16)
+        x = torch.as_tensor(xh).cuda()
+        y = torch.full((a.m,), np.nan, dtype=torch.float64, device="cuda")
+        sp.spmv_csr_run_noalloc(d, x, y)
+        y = y.cpu().numpy()
+        assert np.array_equal(y.view(np.int64), oracle.csr_spmv(a, xh).view(np.int64)), (a.name, call)
+        assert np.array_equal(y.view(np.int64), sp.spmv_run(h, x).cpu().numpy().view(np.int64)), (a.name, call)
 
 
 def test_noalloc_rejects_oversize(sp):
