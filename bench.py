@@ -8,7 +8,13 @@ step's two kernels are captured once as a CUDA graph that every timed step
 replays (--no-graph launches them directly).  Every format is also timed on
 its own; conversions are timed once.  Between timed steps a 256 MiB buffer is
 written to flush L2, and each step is bracketed by CUDA events on the stream
-the kernels run on.
+the kernels run on.  Every row of the timed result is checked against the
+oracle.
+
+The default workload is the largest single-GPU one, the 27-point stencil on
+224^3 (300.8 M nonzeros); the 2e6-row power-law matrix and the 2e7-row
+power-law graph are then measured the same way with fewer steps and carried
+in the same line under "extra_workloads".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...     # the CPU oracle on the host cores
@@ -173,22 +179,6 @@ class ClockSampler:
         reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
         return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
                 "reasons": reasons, "samples": len(rows)}
-
-
-def cpu_leg(a, x, y_gpu, seconds: float):
-    """The CPU-baseline leg: the oracle as it stands (single thread, CSR order)
-    timed on the full matrix, and the timed GPU result checked on 2048 rows
-    against the oracle's definition."""
-    import oracle
-    import synth
-
-    rows = np.linspace(0, a.m - 1, 2048).astype(np.int64)
-    lens = (a.ptr[rows + 1] - a.ptr[rows]).astype(np.int64)
-    sub = synth.CSR(len(rows), a.n, np.concatenate([[0], np.cumsum(lens)]).astype(np.int32),
-                    np.concatenate([a.idx[a.ptr[r]:a.ptr[r + 1]] for r in rows]),
-                    np.concatenate([a.val[a.ptr[r]:a.ptr[r + 1]] for r in rows]))
-    ok = bool(np.all(np.abs(y_gpu[rows] - oracle.csr_spmv(sub, x)) <= oracle.fp_bound(sub, x)))
-    return cpu_oracle_rate(a, x, seconds), {"sampled_rows_within_bound": ok, "rows": len(rows)}
 
 
 def host_cores() -> int:
@@ -414,13 +404,256 @@ def run_batch(args, rank: int, world: int) -> None:
         dist.destroy_process_group()
 
 
+def load_peaks() -> tuple:
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = {}
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            peaks = json.load(fh)
+    peak = peaks.get("hbm_gbs")
+    return (peak, "measured") if peak else (6800.0, "fallback")
+
+
+def load_traffic(key: str):
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as fh:
+            return json.load(fh).get(key)
+    return None
+
+
+class Workload:
+    """One matrix resident in HBM, measured the way the headline step runs:
+    every format converted and timed on its own (the exhaustive search, also
+    the selector's judge), the selector's pick and its autotuned parameters,
+    the step (selector kernel + product, one CUDA graph) timed with the L2
+    flushed before every step, the product kernel's own duration, the gather
+    ceiling of the matrix's index stream, and every row of the result checked
+    against the oracle."""
+
+    def __init__(self, name, args, sp, torch, stream, flush, model, format_steps):
+        import synth
+
+        self.name, self.sp, self.torch, self.stream, self.flush = name, sp, torch, stream, flush
+        self.a = a = make_matrix(name)
+        self.xh = synth.vector(a.n, 1)
+        self.d = sp.DeviceCSR.from_host(a)
+        self.x = torch.as_tensor(self.xh).cuda()
+        self.y = torch.empty(a.m, dtype=torch.float64, device="cuda")
+        self.model = model
+        self.format_steps = format_steps
+        self.args = args
+
+    def timed(self, fn, n, warm):
+        torch, flush, stream = self.torch, self.flush, self.stream
+        for _ in range(warm):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for s, e in evs:
+            flush.zero_()
+            s.record(stream)
+            fn()
+            e.record(stream)
+        torch.cuda.synchronize()
+        return [s.elapsed_time(e) for s, e in evs]
+
+    def setup(self):
+        """Conversions, per-format times, selection, gather ceiling, tuning."""
+        sp, torch, a, d, x, y, args = self.sp, self.torch, self.a, self.d, self.x, self.y, self.args
+        # Each format is converted twice: the first call also pays one-time
+        # costs (loading the kernels on first launch), the second is the steady
+        # cost ("conversion_ms"; the first in "conversion_first_ms").
+        fmts = [int(f) for f in args.formats.split(",") if f != ""]
+        handles, infos, conv_ms, conv_first_ms, status = {}, {}, {}, {}, {}
+        for f in fmts:
+            params = {"max_bytes": int(args.ell_cap_gb * (1 << 30))} if f == 2 else None
+            h = None
+            try:
+                for rep in range(2):
+                    h = None
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    h = sp.spmv_convert(f, d, params)
+                    torch.cuda.synchronize()
+                    (conv_first_ms if rep == 0 else conv_ms)[FORMATS[f]] = 1e3 * (time.perf_counter() - t0)
+            except sp.SpmvError as e:
+                status[FORMATS[f]] = e.name
+                continue
+            handles[f], infos[f] = h, h.info()
+        per_fmt = {}
+        for f, h in handles.items():
+            ms = statistics.mean(self.timed(lambda h=h: sp.spmv_run(h, x, y), self.format_steps, 5))
+            ab = algorithmic_bytes(f, infos[f])
+            per_fmt[FORMATS[f]] = {"ms": ms, "gflops": 2 * a.nnz / ms / 1e6, "alg_gbs": ab / ms / 1e6,
+                                   "alg_bytes": ab, "device_bytes": infos[f]["device_bytes"],
+                                   "params": {k: v for k, v in infos[f]["params"].items() if k != "max_bytes"}}
+        for name, st in status.items():
+            per_fmt[name] = {"status": st}
+        best = min((f for f in handles), key=lambda f: per_fmt[FORMATS[f]]["ms"])
+
+        # ---- selector: the network's own pick; should it name a format whose
+        # conversion failed here, the step runs the exhaustive best instead and
+        # the line says so (the pick still scores 0 % of best, as an infeasible
+        # format does in the corpus evaluation)
+        self.fmt_dev = torch.zeros(1, dtype=torch.int32, device="cuda")
+        feat = torch.empty(16, dtype=torch.float32, device="cuda")
+        model = self.model
+        if model is not None:
+            pick = sp.spmv_select(d, model)
+            fell_back = pick not in handles
+            chosen = best if fell_back else pick
+            self.select_step = lambda: sp.spmv_select_async(d, model, self.fmt_dev)  # noqa: E731
+            kind = "mlp"
+        else:
+            pick, fell_back, chosen = best, False, best
+            self.select_step = lambda: sp.spmv_features(d, feat)  # noqa: E731
+            kind = "exhaustive (no trained model found; the step runs the features kernel)"
+        sel_ms = statistics.mean(self.timed(self.select_step, self.format_steps, 5))
+        pick_ms = per_fmt.get(FORMATS[pick], {}).get("ms")
+        self.selector = {"kind": kind, "pick": FORMATS[pick], "chosen": FORMATS[chosen], "best": FORMATS[best],
+                         "fell_back": fell_back,
+                         "pct_of_best": (100.0 * per_fmt[FORMATS[best]]["ms"] / pick_ms) if pick_ms else 0.0,
+                         "select_us": 1e3 * sel_ms, "select_frac_of_spmv": sel_ms / per_fmt[FORMATS[chosen]]["ms"]}
+
+        # ---- gather ceiling of this matrix's index stream: val[k] * x[idx[k]]
+        # for every entry, one gather and one DFMA each, no row structure
+        from paper_1805_11938_gb300 import probe
+
+        probe_part = torch.empty(probe.partials(), dtype=torch.float64, device="cuda")
+        self.probe_ms = statistics.mean(self.timed(lambda: probe.gather(d, x, probe_part), self.format_steps, 5))
+
+        # ---- the selected format's parameters from the autotuner's grid
+        # (one-off setup, like the conversion): the fastest of the default and the grid
+        hc = handles[chosen]
+        tune_runs = max(10, min(self.format_steps, 50))
+        tune_ms = statistics.mean(self.timed(lambda: sp.spmv_run(hc, x, y), tune_runs, 3))
+        tuning = [{"params": "default", "ms": tune_ms}]
+        for p in tuning_grid(chosen):
+            if not p:
+                continue
+            try:
+                h2 = sp.spmv_convert(chosen, d, p)
+            except sp.SpmvError as e:
+                tuning.append({"params": p, "status": e.name})
+                continue
+            t2 = statistics.mean(self.timed(lambda h2=h2: sp.spmv_run(h2, x, y), tune_runs, 3))
+            tuning.append({"params": p, "ms": t2})
+            if t2 < tune_ms:
+                hc, tune_ms = h2, t2
+            del h2
+        # only the tuned handle stays resident (the 119 GB ELL of the power-law
+        # matrix, for one, is released here)
+        del handles
+        torch.cuda.empty_cache()
+        self.hc, self.chosen, self.best = hc, chosen, best
+        self.info_c = hc.info()
+        self.per_fmt, self.tuning = per_fmt, tuning
+        self.conv_ms, self.conv_first_ms = conv_ms, conv_first_ms
+
+    def step(self):
+        self.select_step()
+        self.sp.spmv_run(self.hc, self.x, self.y)
+
+    def capture(self, warmup, use_graph=True):
+        """Warm-up, then the step's two launches captured once as a CUDA graph."""
+        torch = self.torch
+        for _ in range(warmup):
+            self.flush.zero_()
+            self.step()
+        torch.cuda.synchronize()
+        self.graph = None
+        if use_graph:
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self.step()
+            torch.cuda.synchronize()
+            for _ in range(warmup):
+                self.flush.zero_()
+                self.graph.replay()
+        return self.graph.replay if self.graph is not None else self.step
+
+    def kernel_pass(self, n):
+        """The product kernel's own duration for the roofline: the steps once
+        more, launched directly with an event between the two kernels (an event
+        there delays the second launch by a few microseconds, so it stays out
+        of the headline loop)."""
+        torch, stream = self.torch, self.stream
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for s, mid, e in ev:
+            self.flush.zero_()
+            s.record(stream)
+            self.select_step()
+            mid.record(stream)
+            self.sp.spmv_run(self.hc, self.x, self.y)
+            e.record(stream)
+        torch.cuda.synchronize()
+        return [m.elapsed_time(e) for _, m, e in ev], statistics.mean(s.elapsed_time(e) for s, _, e in ev)
+
+    def roofline(self, kms):
+        peak, src = load_peaks()
+        ab = algorithmic_bytes(self.chosen, self.info_c)
+        achieved = ab / kms / 1e6
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": load_traffic(f"{self.name}:{FORMATS[self.chosen]}"),
+                "kernel": f"{FORMATS[self.chosen]} product", "kernel_ms": kms,
+                "kernel_ms_source": "CUDA events around the product in a second pass of the same steps",
+                "alg_bytes_per_launch": ab, "peak_source": f"{src} hbm_gbs (STREAM-style copy, burst)",
+                "gather_ceiling": {"ms": self.probe_ms, "g_gathers_per_s": self.a.nnz / self.probe_ms / 1e6,
+                                   "frac": self.probe_ms / kms,
+                                   "what": "the gather probe on this matrix's idx/val: one random gather and one "
+                                           "DFMA per entry, no row structure, L2 flushed; frac = its time / the "
+                                           "product's"}}
+
+    def check_all_rows(self):
+        """Every row of the timed steps' y against the oracle, within the FP64 bound."""
+        import oracle
+
+        yv = self.y.cpu().numpy()
+        ref = oracle.csr_spmv_threads(self.a, self.xh, host_cores())
+        bound = oracle.fp_bound(self.a, self.xh)
+        bad = ~(np.abs(yv - ref) <= bound)
+        return {"rows": int(self.a.m), "rows_outside_bound": int(bad.sum()), "all_within_bound": not bool(bad.any()),
+                "against": "oracle (CPU, rows split over the host cores)"}
+
+    def summary(self, step_ms, kms):
+        tuned = {k: v for k, v in self.info_c["params"].items() if k != "max_bytes"}
+        return {"description": WORKLOADS[self.name], "n": self.a.m, "nnz": self.a.nnz,
+                "selected_format": FORMATS[self.chosen], "exhaustive_best": FORMATS[self.best],
+                "selected_params": tuned, "step_ms": step_ms, "gflops": 2.0 * self.a.nnz / step_ms / 1e6,
+                "roofline": self.roofline(kms), "formats": self.per_fmt, "selector": self.selector,
+                "tuning": self.tuning, "conversion_ms": self.conv_ms}
+
+
+def measure_extra(name, args, sp, torch, stream, flush, model) -> dict:
+    """A further workload on the same GPU, after the headline: the same
+    measurements with fewer steps (carried in the JSON line as an extra key)."""
+    w = Workload(name, args, sp, torch, stream, flush, model, max(20, min(args.format_steps, 100)))
+    w.setup()
+    run_step = w.capture(3)
+    n = max(20, min(args.steps, 300))
+    step_ms = statistics.mean(w.timed(run_step, n, 3))
+    kern, _ = w.kernel_pass(n)
+    out = w.summary(step_ms, statistics.mean(kern))
+    out["steps"] = n
+    out["check"] = w.check_all_rows()
+    del w
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="powerlaw_2e6", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="stencil27_224", choices=sorted(WORKLOADS))
+    ap.add_argument("--extras", default=None,
+                    help="comma-separated further workloads measured after the headline and reported as extra keys "
+                         "(default: powerlaw_2e6,graph_2e7 beside the stencil; '' for none)")
     ap.add_argument("--ell-cap-gb", type=float, default=160.0, help="ELL footprint cap (the 2e6 power-law ELL is ~119 GB)")
     ap.add_argument("--format-steps", type=int, default=300)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -439,6 +672,12 @@ def main():
     if args.workload == "batch512":
         run_batch(args, rank, world)
         return
+    if args.extras is None:
+        args.extras = "powerlaw_2e6,graph_2e7" if args.workload == "stencil27_224" else ""
+    extras = [e for e in args.extras.split(",") if e]
+    for e in extras:
+        if e not in WORKLOADS or e == "batch512":
+            raise SystemExit(f"unknown extra workload {e}")
 
     import torch
 
@@ -455,134 +694,22 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    import synth
     import paper_1805_11938_gb300 as sp
 
     sp.lib()
-    a = make_matrix(args.workload)
-    xh = synth.vector(a.n, 1)
-    d = sp.DeviceCSR.from_host(a)
-    x = torch.as_tensor(xh).cuda()
-    y = torch.empty(a.m, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    model = sp.Model.load(sp.MODEL_PATH) if os.path.exists(sp.MODEL_PATH) else None
 
-    # ---- conversions and handles.  Each format is converted twice: the first
-    # call also pays one-time costs (loading the kernels on first launch), the
-    # second is the steady cost ("conversion_ms"; the first in
-    # "conversion_first_ms").  The first handle is freed before the second.
-    fmts = [int(f) for f in args.formats.split(",") if f != ""]
-    handles, infos, conv_ms, conv_first_ms, status = {}, {}, {}, {}, {}
-    for f in fmts:
-        params = {"max_bytes": int(args.ell_cap_gb * (1 << 30))} if f == 2 else None
-        h = None
-        try:
-            for rep in range(2):
-                h = None
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                h = sp.spmv_convert(f, d, params)
-                torch.cuda.synchronize()
-                (conv_first_ms if rep == 0 else conv_ms)[FORMATS[f]] = 1e3 * (time.perf_counter() - t0)
-        except sp.SpmvError as e:
-            status[FORMATS[f]] = e.name
-            continue
-        handles[f], infos[f] = h, h.info()
-
-    def timed(fn, n, warm):
-        for _ in range(warm):
-            flush.zero_()
-            fn()
-        torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
-        for s, e in evs:
-            flush.zero_()
-            s.record(stream)
-            fn()
-            e.record(stream)
-        torch.cuda.synchronize()
-        return [s.elapsed_time(e) for s, e in evs]
-
-    # ---- every format on its own (exhaustive search, also the selector's judge)
-    per_fmt = {}
-    for f, h in handles.items():
-        ms = statistics.mean(timed(lambda h=h: sp.spmv_run(h, x, y), args.format_steps, 5))
-        ab = algorithmic_bytes(f, infos[f])
-        per_fmt[FORMATS[f]] = {"ms": ms, "gflops": 2 * a.nnz / ms / 1e6, "alg_gbs": ab / ms / 1e6,
-                               "alg_bytes": ab, "device_bytes": infos[f]["device_bytes"],
-                               "params": {k: v for k, v in infos[f]["params"].items() if k != "max_bytes"}}
-    for name, st in status.items():
-        per_fmt[name] = {"status": st}
-    best = min((f for f in handles), key=lambda f: per_fmt[FORMATS[f]]["ms"])
-
-    # ---- selector
-    model = None
-    if os.path.exists(sp.MODEL_PATH):
-        model = sp.Model.load(sp.MODEL_PATH)
-    fmt_dev = torch.zeros(1, dtype=torch.int32, device="cuda")
-    feat = torch.empty(16, dtype=torch.float32, device="cuda")
-    if model is not None:
-        chosen = sp.spmv_select(d, model)
-        if chosen not in handles:
-            chosen = best
-        select_step = lambda: sp.spmv_select_async(d, model, fmt_dev)  # noqa: E731
-        selector_kind = "mlp"
-    else:
-        chosen = best
-        select_step = lambda: sp.spmv_features(d, feat)  # noqa: E731
-        selector_kind = "exhaustive (no trained model found; the step runs the features kernel)"
-    sel_ms = statistics.mean(timed(select_step, args.format_steps, 5))
-
-    # ---- gather ceiling of this matrix's index stream: val[k] * x[idx[k]] for
-    # every entry, one gather and one DFMA each, no row structure
-    from paper_1805_11938_gb300 import probe
-
-    probe_part = torch.empty(probe.partials(), dtype=torch.float64, device="cuda")
-    probe_ms = statistics.mean(timed(lambda: probe.gather(d, x, probe_part), args.format_steps, 5))
-    # ---- the selected format's parameters from the autotuner's grid (one-off
-    # setup, like the conversion): the fastest of the default and the grid
-    hc = handles[chosen]
-    tune_runs = max(10, min(args.format_steps, 50))
-    tune_ms = statistics.mean(timed(lambda: sp.spmv_run(hc, x, y), tune_runs, 3))
-    tuning = [{"params": "default", "ms": tune_ms}]
-    for p in tuning_grid(chosen):
-        if not p:
-            continue
-        try:
-            h2 = sp.spmv_convert(chosen, d, p)
-        except sp.SpmvError as e:
-            tuning.append({"params": p, "status": e.name})
-            continue
-        t2 = statistics.mean(timed(lambda h2=h2: sp.spmv_run(h2, x, y), tune_runs, 3))
-        tuning.append({"params": p, "ms": t2})
-        if t2 < tune_ms:
-            hc, tune_ms = h2, t2
-        del h2
-    info_c = hc.info()
-    tuned_params = {k: v for k, v in info_c["params"].items() if k != "max_bytes"}
-
-    def step():
-        select_step()
-        sp.spmv_run(hc, x, y)
+    w = Workload(args.workload, args, sp, torch, stream, flush, model, args.format_steps)
+    w.setup()
+    a, x, y, xh = w.a, w.x, w.y, w.xh
 
     # ---- timed steps (the headline).  The step's two launches (the selector
     # kernel, the product) are captured once as a CUDA graph and the graph is
     # replayed every step: each replay runs both kernels in full, without the
     # host between them.
-    for _ in range(args.warmup):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    graph = None
-    if not args.no_graph:
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            step()
-        torch.cuda.synchronize()
-        for _ in range(args.warmup):
-            flush.zero_()
-            graph.replay()
-    run_step = graph.replay if graph is not None else step
+    run_step = w.capture(args.warmup, not args.no_graph)
     barrier()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
@@ -598,22 +725,8 @@ def main():
     step_ms = [s.elapsed_time(e) for s, e in ev]
     total_ms, value = reduce_over_ranks(sum(step_ms), 2.0 * a.nnz * args.steps, dist, "cuda")
     clocks = clk.summary()
-    # The product kernel's own duration for the roofline: the same steps once
-    # more, launched directly with an event between the two kernels (an event
-    # there delays the second launch by a few microseconds, so it stays out of
-    # the headline loop).
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for s, mid, e in ev:
-        flush.zero_()
-        s.record(stream)
-        select_step()
-        mid.record(stream)
-        sp.spmv_run(hc, x, y)
-        e.record(stream)
-    torch.cuda.synchronize()
-    kern_ms = [m.elapsed_time(e) for _, m, e in ev]
-    eager_step_ms = statistics.mean(s.elapsed_time(e) for s, _, e in ev)
+    kern_ms, eager_step_ms = w.kernel_pass(args.steps)
+    check = w.check_all_rows() if rank == 0 else None
 
     # ---- end to end: every step copies its x in from pinned host memory, runs
     # the step through the library, and copies its y out.  x and y are
@@ -644,8 +757,8 @@ def main():
             stream.wait_event(ev[i][0])
             if i >= 2:
                 stream.wait_event(ev[i - 2][2])  # buffer b's previous y has been copied out
-            select_step()
-            sp.spmv_run(hc, xb[b], yb[b])
+            w.select_step()
+            sp.spmv_run(w.hc, xb[b], yb[b])
             ev[i][1].record(stream)
             with torch.cuda.stream(s_out):
                 s_out.wait_event(ev[i][1])
@@ -660,71 +773,45 @@ def main():
     e2e_ms = e2e_run(n_e2e)
     torch.cuda.synchronize()
     e2e_same = bool(np.array_equal(yh_pin[(n_e2e - 1) % 2].numpy(), y.cpu().numpy()))
-
-    yv = y.cpu().numpy()
     agree = None
     if model is not None:
         torch.cuda.synchronize()
-        agree = int(fmt_dev.item()) == chosen
+        agree = FORMATS[int(w.fmt_dev.item())] == w.selector["pick"]
+    del xb, yb, xh_pin, yh_pin
 
-    # ---- roofline of the dominant kernel (the chosen format's product)
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        with open(pk) as fh:
-            peaks = json.load(fh)
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
     kms = statistics.mean(kern_ms)
-    ab = algorithmic_bytes(chosen, info_c)
-    achieved = ab / kms / 1e6
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        with open(tr_path) as fh:
-            tr = json.load(fh)
-        key = f"{args.workload}:{FORMATS[chosen]}"
-        if key in tr:
-            traffic = tr[key]
-
+    summ = w.summary(total_ms / args.steps, kms)
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": a.m, "nnz": a.nnz,
-                   "selected_format": FORMATS[chosen], "exhaustive_best": FORMATS[best], "selector": selector_kind,
-                   "selected_params": tuned_params, "tuning": tuning,
+                   "selected_format": summ["selected_format"], "exhaustive_best": summ["exhaustive_best"],
+                   "selector": w.selector["kind"], "selected_params": summ["selected_params"], "tuning": w.tuning,
                    "step": "selector kernel + SpMV in the selected format, matrix and x resident in HBM",
                    "launch": ("the step's two kernels captured once as a CUDA graph, replayed every step"
-                              if graph is not None else "the step's two kernels launched directly"),
+                              if w.graph is not None else "the step's two kernels launched directly"),
                    "direct_launch_step_ms": eager_step_ms,
                    "l2": "flushed: 256 MiB written before every timed step", "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": f"{FORMATS[chosen]} product", "kernel_ms": kms,
-                     "kernel_ms_source": "CUDA events around the product in a second pass of the same steps",
-                     "alg_bytes_per_launch": ab, "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy, burst)",
-                     "gather_ceiling": {"ms": probe_ms, "g_gathers_per_s": a.nnz / probe_ms / 1e6,
-                                        "frac": probe_ms / kms,
-                                        "what": "spmv_probe_gather on this matrix's idx/val: one random gather and "
-                                                "one DFMA per entry, no row structure, L2 flushed; frac = its time / "
-                                                "the product's"}},
+        "roofline": summ["roofline"],
         "e2e": {"value": 2.0 * a.nnz / e2e_ms / 1e6, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * a.n,
                 "d2h_bytes_per_step": 8 * a.m, "ms_per_step": e2e_ms, "steps": n_e2e,
                 "copies": "pinned host x in and y out every step, double-buffered on two copy streams "
                           "(overlapping the neighbouring steps' compute)", "y_matches_device_run": e2e_same},
-        "gpu_launches": args.steps * (1 + launches_per_run(chosen, info_c)),
+        "gpu_launches": args.steps * (1 + launches_per_run(w.chosen, w.info_c)),
         "clocks": clocks,
-        "formats": per_fmt,
-        "selector": {"kind": selector_kind, "chosen": FORMATS[chosen], "best": FORMATS[best],
-                     "pct_of_best": 100.0 * per_fmt[FORMATS[best]]["ms"] / per_fmt[FORMATS[chosen]]["ms"],
-                     "select_us": 1e3 * sel_ms, "select_frac_of_spmv": sel_ms / per_fmt[FORMATS[chosen]]["ms"],
-                     "per_step_agrees": agree},
-        "conversion_ms": conv_ms, "conversion_first_ms": conv_first_ms,
+        "formats": w.per_fmt,
+        "selector": dict(w.selector, per_step_agrees=agree),
+        "conversion_ms": w.conv_ms, "conversion_first_ms": w.conv_first_ms,
         "wall_s_timed_region": t_wall,
+        "check": check,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"], line["check"] = cpu_leg(a, xh, yv, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_oracle_rate(a, xh, args.cpu_seconds)
+    del w
+    torch.cuda.empty_cache()
+    if rank == 0 and extras:
+        line["extra_workloads"] = {e: measure_extra(e, args, sp, torch, stream, flush, model) for e in extras}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
