@@ -181,24 +181,40 @@ SPMV_API void spmv_free(spmv_handle* h);
  * 3 min, 4 max, 5 mean, 6 std of the row length, 7 std/mean, 8 log2 nnz,
  * 9 mean/max, 10 HYB tail fraction, 11 mean and 12 max |col - row| over each
  * row's first 16 entries, 13 empty-row fraction, 14 fraction of rows of length
- * >= 32, 15 SELL-32 fill; the statistics are over rows floor(k*M/8192),
- * k < 8192, when M > 8192 (all rows otherwise), so the cost does not grow
+ * >= 32, 15 SELL-32 fill.  Features 3-7, 9, 13 and 14 are exact over all M
+ * rows (one pass over ptr); 10, 11, 12 and 15 come from rows floor(k*M/8192),
+ * k < 8192, when M > 8192 (all rows otherwise), so their cost does not grow
  * with M.  csr->idx holds csr->nnz entries and needs no particular alignment.
  * The CSR must be well formed (ptr[0] = 0, non-decreasing, ptr[M] = nnz, as
- * spmv_convert checks); this call does not check it.  One kernel launch (a
- * thread-block cluster), asynchronous. */
+ * spmv_convert checks); this call does not check it.  Two kernel launches
+ * (the pass over ptr, then a thread-block cluster), asynchronous.  The pass
+ * over ptr reduces into one slot of a small static device array of the
+ * library (64 slots per device, taken in turn by the calls): at most 64
+ * features or selection calls may be in flight on one device at once, and a
+ * CUDA graph that captured such a call replays its slot, so replays of that
+ * graph must not overlap each other on the GPU.  The first call on a device
+ * looks up the array's address; make it before any stream capture. */
 SPMV_API int spmv_features(const spmv_csr* csr, float* feat_dev, cudaStream_t stream);
 
 /* A trained selector: network parameters (SPMV_MLP_PARAMS floats, W1, b1, W2,
  * b2, W3, b3 row-major) and the per-feature minimum and maximum of the
  * transformed training features (Sec. V-B "Feature Scaling"), host arrays
- * copied to the device. */
+ * copied to the device.  The model's footprint cap for selection (see
+ * spmv_select_async) starts at 90% of the device memory free at creation. */
 SPMV_API int spmv_model_create(const float* params_host, const float* lo_host, const float* hi_host, spmv_model** out);
 SPMV_API void spmv_model_free(spmv_model* m);
 
-/* Features + scaling + network + argmax in one launch (Sec. V-A deployment:
- * features in, representation label out).  Writes the format id to
- * fmt_dev[0] and, if logits_dev is not NULL, the 5 logits.  Asynchronous. */
+/* Sets the model's footprint cap for selection, in bytes (> 0). */
+SPMV_API int spmv_model_set_max_bytes(spmv_model* m, int64_t max_bytes);
+
+/* Features + scaling + network + argmax (Sec. V-A deployment: features in,
+ * representation label out), the launches of spmv_features.  Writes the
+ * format id to fmt_dev[0] and, if logits_dev is not NULL, the 5 logits.
+ * The argmax never names ELL when ELL's padded layout (ceil(M/4)*4 rows of
+ * max-row-length slots of 12 bytes, plus 4 bytes per row; exact, from the
+ * longest row) exceeds the model's cap: it is then taken over the other
+ * four formats, whose layouts stay within a small multiple of the CSR's.
+ * Asynchronous. */
 SPMV_API int spmv_select_async(const spmv_csr* csr, const spmv_model* model, int32_t* fmt_dev, float* logits_dev,
                       cudaStream_t stream);
 

@@ -5,31 +5,32 @@ profiling -- n_rows, n_cols, nnz_frac, nnz_min, nnz_max, nnz_avg, nnz_std and
 "variation".  Eight more are added for the GPU formats.  Definitions (the paper
 gives names only; the readings are ours):
 
-Row sample R: all rows if M <= 8192, else rows floor(k*M/8192), k < 8192.
-len_i = ptr[i+1] - ptr[i];  L = sum over R of len_i;  |R| = count.
+len_i = ptr[i+1] - ptr[i] over all rows i < M; nnz = ptr[M] = sum of len_i.
+Row sample R (for features 10, 11, 12 and 15 only): all rows if M <= 8192,
+else rows floor(k*M/8192), k < 8192; L = sum over R of len_i.
 
  0 n_rows      M
  1 n_cols      N
- 2 nnz_frac    nnz / (M*N)                     (nnz = ptr[M], exact)
- 3 nnz_min     min over R of len_i
- 4 nnz_max     max over R of len_i
- 5 nnz_avg     nnz / M                         (exact)
- 6 nnz_std     population std of len over R:  sqrt(|R|*sum len^2 - L^2) / |R|
- 7 variation   nnz_std / (L/|R|), 0 if L = 0   (coefficient of variation)
+ 2 nnz_frac    nnz / (M*N)
+ 3 nnz_min     min over all rows of len_i
+ 4 nnz_max     max over all rows of len_i
+ 5 nnz_avg     nnz / M
+ 6 nnz_std     population std of len over all rows: sqrt(M*sum len^2 - nnz^2) / M
+ 7 variation   nnz_std / nnz_avg, 0 if nnz = 0  (coefficient of variation)
  8 log2_nnz    log2(max(nnz, 1))
- 9 ell_fill    (L/|R|) / nnz_max, 0 if nnz_max = 0
+ 9 ell_fill    nnz_avg / nnz_max, 0 if nnz_max = 0
 10 hyb_tail    sum over R of max(0, len_i - K) / L, 0 if L = 0, where K is the
                HYB rule on R with lengths capped at 512: the largest
                k in [1, 512] with #{len_i >= k} >= ceil(|R|/3), else 0
 11 diag_spread mean |col - i| over the first min(len_i, 16) entries of each
                sampled row (0 if none)
 12 bandwidth   max |col - i| over the same entries
-13 empty_frac  #{len_i = 0} / |R|
-14 long_frac   #{len_i >= 32} / |R|
+13 empty_frac  #{len_i = 0} / M
+14 long_frac   #{len_i >= 32} / M
 15 sell32_fill fill of SELL-32 with rows sorted over all of R, lengths capped
                at 512: sum min(len_i, 512) / (32 * sum_{k=1..512} ceil(c_k/32)),
-               c_k = #{len_i >= k}; 1 if the denominator is 0.  (Slice s of the
-               descending order has width >= k exactly when 32*s < c_k.)
+               c_k = #{len_i >= k} over R; 1 if the denominator is 0.  (Slice s
+               of the descending order has width >= k exactly when 32*s < c_k.)
 """
 from __future__ import annotations
 
@@ -74,14 +75,17 @@ def features(a) -> np.ndarray:
     m, n = a.m, a.n
     ptr = [int(v) for v in a.ptr]
     nnz = ptr[m]
+    # whole-matrix row-length statistics, exact integers (the sum of squares is
+    # at most nnz * max len < 2^62, so int64 holds it)
+    all_lens = np.diff(np.asarray(a.ptr, dtype=np.int64))
+    sq = int(np.sum(all_lens * all_lens))
+    std = math.sqrt(m * sq - nnz * nnz) / m  # Python integers, one rounding inside sqrt's argument
+    mean = nnz / m
+    mx = int(all_lens.max())
+    # the sampled rows
     rows = sample_rows(m)
     lens = [ptr[i + 1] - ptr[i] for i in rows]
-    cnt = len(lens)
     L = sum(lens)
-    sq = sum(l * l for l in lens)
-    std = math.sqrt(cnt * sq - L * L) / cnt  # exact integers, one rounding inside sqrt's argument
-    mean_s = L / cnt
-    mx = max(lens)
     K = hyb_k_of_lengths(lens, LEN_CAP)
     tail = sum(max(0, l - K) for l in lens)
     spread_sum, spread_cnt, band = 0, 0, 0
@@ -103,18 +107,18 @@ def features(a) -> np.ndarray:
         float(m),
         float(n),
         nnz / (m * n),
-        float(min(lens)),
+        float(all_lens.min()),
         float(mx),
-        nnz / m,
+        mean,
         std,
-        std / mean_s if L > 0 else 0.0,
+        std / mean if nnz > 0 else 0.0,
         math.log2(max(nnz, 1)),
-        mean_s / mx if mx > 0 else 0.0,
+        mean / mx if mx > 0 else 0.0,
         tail / L if L > 0 else 0.0,
         spread_sum / spread_cnt if spread_cnt > 0 else 0.0,
         float(band),
-        sum(1 for l in lens if l == 0) / cnt,
-        sum(1 for l in lens if l >= LONG_ROW) / cnt,
+        int(np.count_nonzero(all_lens == 0)) / m,
+        int(np.count_nonzero(all_lens >= LONG_ROW)) / m,
         capped / (32 * slice_widths) if slice_widths > 0 else 1.0,
     ]
     return np.array(f, dtype=np.float64)

@@ -208,6 +208,10 @@ class Model:
     def raw(self):
         return self._m
 
+    def set_max_bytes(self, max_bytes: int) -> None:
+        """Footprint cap for selection: spmv_select never names ELL above it."""
+        check(lib().spmv_model_set_max_bytes(self._m, int(max_bytes)), "spmv_model_set_max_bytes")
+
     @classmethod
     def load(cls, path: str) -> "Model":
         import json

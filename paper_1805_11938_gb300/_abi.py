@@ -68,6 +68,7 @@ _SIGS = {
     "spmv_features": (ctypes.c_int, [ctypes.POINTER(spmv_csr), _VP, _VP]),
     "spmv_model_create": (ctypes.c_int, [_VP, _VP, _VP, ctypes.POINTER(_VP)]),
     "spmv_model_free": (None, [_VP]),
+    "spmv_model_set_max_bytes": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "spmv_select_async": (ctypes.c_int, [ctypes.POINTER(spmv_csr), _VP, _VP, _VP, _VP]),
     "spmv_select": (ctypes.c_int, [ctypes.POINTER(spmv_csr), _VP, _VP, ctypes.POINTER(ctypes.c_int)]),
     "spmv_mlp_scale": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP, _VP]),

@@ -3,25 +3,39 @@
 // representation label out; here a 16-64-64-5 multilayer perceptron, one of
 // the alternatives of Sec. V-D), with its training kernels.
 //
-// Feature definitions (rows sampled when M > 8192):
-//   R = all rows, or rows floor(k*M/8192) for k < 8192; len_i = ptr[i+1]-ptr[i]
-//   0 n_rows  1 n_cols  2 nnz/(M*N)  3 min len  4 max len  5 nnz/M
-//   6 std of len over R  7 std/mean  8 log2(max(nnz,1))  9 mean/max
-//  10 HYB tail fraction with K from R (lengths capped at 512)
+// Feature definitions (len_i = ptr[i+1] - ptr[i]; the row-length statistics
+// are exact over all M rows, the histogram and index statistics come from a
+// row sample R = all rows, or rows floor(k*M/8192) for k < 8192):
+//   0 n_rows  1 n_cols  2 nnz/(M*N)  3 min len  4 max len  5 mean = nnz/M
+//   6 std of len  7 std/mean  8 log2(max(nnz,1))  9 mean/max
+//  10 HYB tail fraction over R with K from R (lengths capped at 512)
 //  11 mean |col-row| and 12 max |col-row| over the first 16 entries of each sampled row
 //  13 fraction of empty rows  14 fraction of rows with len >= 32
 //  15 SELL-32 fill over R sorted, lengths capped at 512
 //
-// The features kernel is one thread-block cluster (16 CTAs x 512 threads where
-// the device can place one, else 8 x 1024), one sampled row per thread.  Each
-// CTA reduces its rows, then adds its statistics and its length histogram
-// into CTA 0's shared memory with cluster shared-memory atomics (no global
-// scratch); after one cluster barrier two warps of CTA 0 finish: warp 1 scans
-// the histogram while warp 0 evaluates the features as straight-line code,
-// then, for a selection, both run the network.  A lone warp's dependent
-// instructions are the cost there, so that code avoids divergent per-feature
-// branches and keeps its divisions independent.
+// Two launches.  k_rowstats reads ptr once with the whole GPU and reduces the
+// exact statistics (min, max, sum of squares, empty rows, rows of length >= 32)
+// into one slot of a small static device array, its last block to finish
+// publishing them.  The features kernel, launched behind it with
+// programmatic stream serialization, is one thread-block cluster (16 CTAs x
+// 512 threads where the device can place one, else 8 x 1024), one sampled row
+// per thread.  Each CTA reduces its rows, then adds its statistics and its
+// length histogram into CTA 0's shared memory with cluster shared-memory
+// atomics; after one cluster barrier two warps of CTA 0 wait for k_rowstats
+// and finish: warp 1 scans the histogram while warp 0 evaluates the features
+// as straight-line code, then, for a selection, both run the network.  A lone
+// warp's dependent instructions are the cost there, so that code avoids
+// divergent per-feature branches and keeps its divisions independent.
+//
+// Selection never returns ELL when its padded layout (ceil(M/4)*4 rows of
+// max-len slots, 12 bytes each, plus the row lengths) would exceed the
+// model's max_bytes: the exact longest row makes that footprint exact, and
+// the argmax is then taken over the other four formats.  The other layouts
+// stay within a small multiple of the CSR (SELL: nnz + C * max-len slots;
+// HYB: K * M <= 3 * nnz slots by the rule for K; CSR5: the CSR padded to
+// whole tiles).
 #include <atomic>
+#include <mutex>
 #include <cooperative_groups.h>
 #include <cuda_pipeline.h>
 
@@ -34,6 +48,7 @@ struct spmv_model {
     float* params = nullptr;  // SPMV_MLP_PARAMS
     float* lo = nullptr;      // 16
     float* hi = nullptr;      // 16
+    int64_t max_bytes = 0;    // selection refuses ELL layouts larger than this
 };
 
 namespace spmv {
@@ -94,9 +109,9 @@ __device__ __forceinline__ float u64_to_f32(unsigned long long v) { return (floa
 // FMA chains stay short (consecutive j: conflict-free weight reads; the inputs
 // are broadcast).  Warp 0 alone computes the five outputs, four lanes each
 // (output c in lanes 4c..4c+3), writes them to z_out if given, and returns in
-// every lane the index of the largest (the first of equal maxima).  Warp 1
-// returns -1 once the second layer is done.
-__device__ int mlp_forward_64(const float* th, const float* xs, float* h1, float* h2, float* z_out) {
+// every lane the index of the largest (the first of equal maxima; ELL only
+// when ell_ok).  Warp 1 returns -1 once the second layer is done.
+__device__ int mlp_forward_64(const float* th, const float* xs, float* h1, float* h2, float* z_out, bool ell_ok = true) {
     const int j = threadIdx.x;
     float a0 = th[oB1 + j], a1 = 0.f;
 #pragma unroll
@@ -139,12 +154,115 @@ __device__ int mlp_forward_64(const float* th, const float* xs, float* h1, float
 #pragma unroll
     for (int q = 1; q < 5; ++q) {
         const float v = __shfl_sync(dev::kFull, zc, 4 * q);
-        if (v > best) {
+        if (v > best && (q != SPMV_ELL || ell_ok)) {
             best = v;
             bi = q;
         }
     }
     return bi;
+}
+
+// ------------------------------------------------------- exact row lengths
+//
+// One slot of the ring holds one call's accumulators (reset to zero by the
+// call's last block, so every call finds them at zero) and its published
+// totals.  Calls take slots in turn on the host, so up to kRowSlots calls may
+// be in flight on one device at once; a CUDA graph replays the slot it
+// captured.  The minimum is accumulated as the maximum of ~len, so that zero
+// is the identity of every accumulator.
+struct __align__(64) RowStatsSlot {
+    unsigned long long acc_sq;
+    unsigned acc_max, acc_cmin, acc_empty, acc_long, ticket, pad0;
+    unsigned long long fin_sq;
+    unsigned fin_max, fin_min, fin_empty, fin_long;
+};
+constexpr int kRowSlots = 64;
+static __device__ RowStatsSlot g_rowstats[kRowSlots];
+
+constexpr int kRowStatsThreads = 256;
+
+template <bool VEC>
+__global__ void __launch_bounds__(kRowStatsThreads) k_rowstats(const int32_t* __restrict__ ptr, int32_t m,
+                                                               RowStatsSlot* __restrict__ slot) {
+    dev::pdl_trigger();  // the features kernel behind this one may start now
+    unsigned mx = 0, cmn = 0, emp = 0, lng = 0;
+    unsigned long long sq = 0;
+    auto add = [&](int32_t len) {
+        const unsigned l = (unsigned)len;
+        mx = max(mx, l);
+        cmn = max(cmn, ~l);
+        sq += (unsigned long long)l * l;
+        emp += l == 0u;
+        lng += l >= 32u;
+    };
+    const int lane = threadIdx.x & 31;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    int64_t tail0 = 0;
+    if constexpr (VEC) {
+        // quad q = rows 4q .. 4q+3 from one 16-byte load of ptr[4q .. 4q+3];
+        // ptr[4q+4] is the next lane's first word (loaded directly by lane 31
+        // and by the last quad)
+        const int64_t nq = (int64_t)m / 4;
+        for (int64_t qb = gt - lane; qb < nq; qb += nt) {  // warp-uniform bound
+            const int64_t q = qb + lane;
+            int4 v = make_int4(0, 0, 0, 0);
+            if (q < nq) v = __ldcs(reinterpret_cast<const int4*>(ptr) + q);
+            int32_t nx = __shfl_down_sync(dev::kFull, v.x, 1);
+            if (q < nq) {
+                if (lane == 31 || q + 1 == nq) nx = __ldcs(ptr + 4 * q + 4);
+                add(v.y - v.x);
+                add(v.z - v.y);
+                add(v.w - v.z);
+                add(nx - v.w);
+            }
+        }
+        tail0 = 4 * nq;
+    }
+    for (int64_t r = tail0 + gt; r < m; r += nt) add(__ldcs(ptr + r + 1) - __ldcs(ptr + r));
+    mx = __reduce_max_sync(dev::kFull, mx);
+    cmn = __reduce_max_sync(dev::kFull, cmn);
+    emp = __reduce_add_sync(dev::kFull, emp);
+    lng = __reduce_add_sync(dev::kFull, lng);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(dev::kFull, sq, o);
+    __shared__ unsigned red[kRowStatsThreads / 32][4];
+    __shared__ unsigned long long red_sq[kRowStatsThreads / 32];
+    const int w = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[w][0] = mx;
+        red[w][1] = cmn;
+        red[w][2] = emp;
+        red[w][3] = lng;
+        red_sq[w] = sq;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    for (int i = 1; i < kRowStatsThreads / 32; ++i) {
+        mx = max(mx, red[i][0]);
+        cmn = max(cmn, red[i][1]);
+        emp += red[i][2];
+        lng += red[i][3];
+        sq += red_sq[i];
+    }
+    {
+        using ref_u = cuda::atomic_ref<unsigned, cuda::thread_scope_device>;
+        using ref_ull = cuda::atomic_ref<unsigned long long, cuda::thread_scope_device>;
+        ref_u(slot->acc_max).fetch_max(mx, cuda::memory_order_relaxed);
+        ref_u(slot->acc_cmin).fetch_max(cmn, cuda::memory_order_relaxed);
+        ref_u(slot->acc_empty).fetch_add(emp, cuda::memory_order_relaxed);
+        ref_u(slot->acc_long).fetch_add(lng, cuda::memory_order_relaxed);
+        ref_ull(slot->acc_sq).fetch_add(sq, cuda::memory_order_relaxed);
+        // release this block's additions; the last block acquires everyone's
+        const unsigned prev = ref_u(slot->ticket).fetch_add(1u, cuda::memory_order_acq_rel);
+        if (prev != gridDim.x - 1) return;
+        slot->fin_max = ref_u(slot->acc_max).exchange(0u, cuda::memory_order_relaxed);
+        slot->fin_min = ~ref_u(slot->acc_cmin).exchange(0u, cuda::memory_order_relaxed);
+        slot->fin_empty = ref_u(slot->acc_empty).exchange(0u, cuda::memory_order_relaxed);
+        slot->fin_long = ref_u(slot->acc_long).exchange(0u, cuda::memory_order_relaxed);
+        slot->fin_sq = ref_ull(slot->acc_sq).exchange(0ull, cuda::memory_order_relaxed);
+        ref_u(slot->ticket).store(0u, cuda::memory_order_relaxed);
+    }
 }
 
 // The features kernel: one cluster of CTAS CTAs, kSample / CTAS threads each,
@@ -154,23 +272,23 @@ __device__ int mlp_forward_64(const float* th, const float* xs, float* h1, float
 template <int CTAS, bool VEC>
 __global__ void __launch_bounds__(kSample / CTAS)
     k_features(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t m, int32_t n, int64_t nnz,
-               float* __restrict__ feat_out, const float* __restrict__ model_params, const float* __restrict__ lo,
-               const float* __restrict__ hi, int32_t* __restrict__ fmt_out, float* __restrict__ logits_out) {
+               const RowStatsSlot* __restrict__ rs, float* __restrict__ feat_out,
+               const float* __restrict__ model_params, const float* __restrict__ lo, const float* __restrict__ hi,
+               int64_t ell_cap, int32_t* __restrict__ fmt_out, float* __restrict__ logits_out) {
     constexpr int T = kSample / CTAS;
     constexpr int NW = T / 32;
     static_assert(kSample == 1 << 13 && T * CTAS == kSample && NW <= 32 && T >= 64, "sample layout");
     cg::cluster_group cluster = cg::this_cluster();
     const unsigned rank = cluster.block_rank();
-    // In CTA 0 these end as the cluster's totals: the length histogram (lengths
-    // capped at 512), sum of len, of len^2 and of |col - row| over the first 16
-    // entries; min and max len, max |col - row|; empty rows, rows with
-    // len >= 32, entries in the spread sums.
+    // In CTA 0 these end as the cluster's totals over the sampled rows: the
+    // length histogram (lengths capped at 512), sum of len and of |col - row|
+    // over the first 16 entries; max |col - row|; entries in the spread sums.
     __shared__ unsigned hist[kLenCap + 1];
-    __shared__ unsigned long long tot_u[3];
-    __shared__ int tot_i[3];
-    __shared__ unsigned tot_c[3];
-    __shared__ unsigned long long red_u[NW][3];
-    __shared__ unsigned red_c[NW][6];
+    __shared__ unsigned long long tot_u[2];
+    __shared__ int tot_band;
+    __shared__ unsigned tot_cnt;
+    __shared__ unsigned long long red_u[NW][2];
+    __shared__ unsigned red_c[NW][2];
     __shared__ float qop[4];
     __shared__ __align__(16) float wsm[kNP + 3 + 32];
     __shared__ int32_t nnz_sm;
@@ -191,10 +309,10 @@ __global__ void __launch_bounds__(kSample / CTAS)
         __pipeline_commit();
     }
     for (int b = tid; b <= kLenCap; b += T) hist[b] = 0;
-    if (tid < 3) {
-        tot_u[tid] = 0;
-        tot_i[tid] = tid == 0 ? 0x7fffffff : 0;
-        tot_c[tid] = 0;
+    if (tid < 2) tot_u[tid] = 0;
+    if (tid == 0) {
+        tot_band = 0;
+        tot_cnt = 0;
     }
     __syncthreads();
     cluster_arrive();  // waited for before the CTAs add into CTA 0's totals
@@ -261,18 +379,14 @@ __global__ void __launch_bounds__(kSample / CTAS)
     }
     {
         const unsigned long long a0 = warp_sum_u64(on ? (unsigned long long)len : 0ull);
-        const unsigned long long a1 = warp_sum_u64(on ? (unsigned long long)len * (unsigned long long)len : 0ull);
         const unsigned long long a2 = warp_sum_u64(ssum);
-        const int i0 = warp_min_i32(on ? len : 0x7fffffff);
-        const int i1 = warp_max_i32(len);
         const int i2 = warp_max_i32(band);
-        const unsigned c0 = warp_sum_u32((unsigned)(on && len == 0));
-        const unsigned c1 = warp_sum_u32((unsigned)(len >= 32));
         const unsigned c2 = warp_sum_u32((unsigned)ne);
         if (lane == 0) {
-            red_u[warp][0] = a0; red_u[warp][1] = a1; red_u[warp][2] = a2;
-            red_c[warp][0] = (unsigned)i0; red_c[warp][1] = (unsigned)i1; red_c[warp][2] = (unsigned)i2;
-            red_c[warp][3] = c0; red_c[warp][4] = c1; red_c[warp][5] = c2;
+            red_u[warp][0] = a0;
+            red_u[warp][1] = a2;
+            red_c[warp][0] = (unsigned)i2;
+            red_c[warp][1] = c2;
         }
     }
     __syncthreads();
@@ -290,21 +404,13 @@ __global__ void __launch_bounds__(kSample / CTAS)
     if (warp == 0) {
         const bool ok = lane < NW;
         const unsigned long long a0 = warp_sum_u64(ok ? red_u[lane][0] : 0ull);
-        const unsigned long long a1 = warp_sum_u64(ok ? red_u[lane][1] : 0ull);
-        const unsigned long long a2 = warp_sum_u64(ok ? red_u[lane][2] : 0ull);
-        const int i0 = warp_min_i32(ok ? (int)red_c[lane][0] : 0x7fffffff);
-        const int i1 = warp_max_i32(ok ? (int)red_c[lane][1] : 0);
-        const int i2 = warp_max_i32(ok ? (int)red_c[lane][2] : 0);
-        const unsigned c0 = warp_sum_u32(ok ? red_c[lane][3] : 0u);
-        const unsigned c1 = warp_sum_u32(ok ? red_c[lane][4] : 0u);
-        const unsigned c2 = warp_sum_u32(ok ? red_c[lane][5] : 0u);
+        const unsigned long long a2 = warp_sum_u64(ok ? red_u[lane][1] : 0ull);
+        const int i2 = warp_max_i32(ok ? (int)red_c[lane][0] : 0);
+        const unsigned c2 = warp_sum_u32(ok ? red_c[lane][1] : 0u);
         unsigned long long* tu = cluster.map_shared_rank(tot_u, 0);
-        int* ti = cluster.map_shared_rank(tot_i, 0);
-        unsigned* tc = cluster.map_shared_rank(tot_c, 0);
-        if (lane < 3) atomicAdd(tu + lane, lane == 0 ? a0 : (lane == 1 ? a1 : a2));
-        else if (lane == 3) atomicMin(ti, i0);
-        else if (lane < 6) atomicMax(ti + (lane - 3), lane == 4 ? i1 : i2);
-        else if (lane < 9) atomicAdd(tc + (lane - 6), lane == 6 ? c0 : (lane == 7 ? c1 : c2));
+        if (lane < 2) atomicAdd(tu + lane, lane == 0 ? a0 : a2);
+        else if (lane == 2) atomicMax(cluster.map_shared_rank(&tot_band, 0), i2);
+        else if (lane == 3) atomicAdd(cluster.map_shared_rank(&tot_cnt, 0), c2);
     }
     cluster.sync();
     if (rank != 0) return;  // CTA 0 holds everything now
@@ -366,24 +472,31 @@ __global__ void __launch_bounds__(kSample / CTAS)
     // takes the one quotient of its own feature, so the correctly rounded
     // divisions run side by side rather than one after another.
     float f = 0.0f;
+    bool ell_ok = true;
     if (warp == 0) {
+        dev::pdl_wait();  // k_rowstats has completed: its totals are visible
         const int j = lane & 15;
-        const unsigned long long sum_len = tot_u[0], sum_sq = tot_u[1], spread_sum = tot_u[2];
-        const int min_len = tot_i[0], max_len = tot_i[1], bandw = tot_i[2];
-        const unsigned empty = tot_c[0], longc = tot_c[1], spread_cnt = tot_c[2];
-        const float fc = (float)cnt;
-        const float L = u64_to_f32(sum_len);
-        const float mean = L / fc;
+        const unsigned long long spread_sum = tot_u[1];
+        const unsigned long long sum_len = (unsigned long long)(unsigned)nnz_sm;  // exact, all rows
+        const unsigned long long sum_sq = rs->fin_sq;
+        const int min_len = (int)rs->fin_min, max_len = (int)rs->fin_max, bandw = tot_band;
+        const unsigned empty = rs->fin_empty, longc = rs->fin_long, spread_cnt = tot_cnt;
+        const unsigned rows = (unsigned)m;
+        const float fc = (float)m;
         const float nz = (float)nnz_sm;
-        // std = sqrt(cnt * sum_sq - L^2) / cnt, the difference in exact 128-bit integer arithmetic
-        const unsigned long long a_lo = (unsigned long long)cnt * sum_sq;
-        const unsigned long long a_hi = __umul64hi((unsigned long long)cnt, sum_sq);
+        const float mean = nz / fc;
+        // std = sqrt(M * sum_sq - nnz^2) / M, the difference in exact 128-bit integer arithmetic
+        const unsigned long long a_lo = (unsigned long long)rows * sum_sq;
+        const unsigned long long a_hi = __umul64hi((unsigned long long)rows, sum_sq);
         const unsigned long long b_lo = sum_len * sum_len;
         const unsigned long long b_hi = __umul64hi(sum_len, sum_len);
         const unsigned long long d_lo = a_lo - b_lo;
         const unsigned long long d_hi = a_hi - b_hi - (a_lo < b_lo ? 1ull : 0ull);
         const float sd = sqrtf(u64_to_f32(d_hi) * 18446744073709551616.0f + u64_to_f32(d_lo)) / fc;
         const float spread = u64_to_f32(spread_sum), spread_n = (float)spread_cnt;
+        // the ELL layout's footprint, exact from the longest row
+        const long long ld = ((long long)m + 3) / 4 * 4;
+        ell_ok = ld * (long long)max_len * 12 + ld * 4 <= (long long)ell_cap;
         const float lg = log2f(nnz_sm > 1 ? nz : 1.0f);
         // numerator and denominator of this lane's quotient (0 / 1 where it has none)
         float num = 0.0f, den = 1.0f;
@@ -421,28 +534,63 @@ __global__ void __launch_bounds__(kSample / CTAS)
     }
     if (!model_params) return;
     tail_sync();
-    const int best = mlp_forward_64(wsm, xs, h1, h2, logits_out);
+    const int best = mlp_forward_64(wsm, xs, h1, h2, logits_out, ell_ok);
     if (tid == 0 && fmt_out) fmt_out[0] = best;
 }
 
+// The features kernel, launched behind k_rowstats with programmatic stream
+// serialization (its sampled part overlaps the exact pass over ptr).
 template <int CTAS, bool VEC>
-static cudaError_t launch_features_k(const spmv_csr* c, float* feat, const spmv_model* model, int32_t* fmt,
-                                     float* logits, cudaStream_t s) {
+static cudaError_t launch_features_k(const spmv_csr* c, const RowStatsSlot* rs, float* feat, const spmv_model* model,
+                                     int32_t* fmt, float* logits, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CTAS, 1, 1);
     cfg.blockDim = dim3(kSample / CTAS, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = CTAS;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_features<CTAS, VEC>, c->ptr, c->idx, c->m, c->n, (int64_t)c->nnz, feat,
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, k_features<CTAS, VEC>, c->ptr, c->idx, c->m, c->n, (int64_t)c->nnz, rs, feat,
                               model ? (const float*)model->params : nullptr, model ? (const float*)model->lo : nullptr,
-                              model ? (const float*)model->hi : nullptr, fmt, logits);
+                              model ? (const float*)model->hi : nullptr, model ? model->max_bytes : (int64_t)0, fmt,
+                              logits);
+}
+
+// This device's ring of row-statistics slots (looked up once per device, with
+// that device current) and the next slot in turn.
+static int rowstats_slot(RowStatsSlot** out) {
+    static std::mutex mu;
+    static RowStatsSlot* base[64] = {};
+    static std::atomic<unsigned> next{0};
+    int dev = 0;
+    SPMV_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return set_error(SPMV_ERR_INVALID_ARG, "device %d out of range", dev);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!base[dev]) {
+            void* p = nullptr;
+            SPMV_CUDA(cudaGetSymbolAddress(&p, g_rowstats));
+            base[dev] = static_cast<RowStatsSlot*>(p);
+        }
+    }
+    *out = base[dev] + (next.fetch_add(1u, std::memory_order_relaxed) % kRowSlots);
+    return SPMV_OK;
+}
+
+static cudaError_t launch_rowstats(const spmv_csr* c, RowStatsSlot* rs, cudaStream_t s) {
+    const bool vec = (reinterpret_cast<uintptr_t>(c->ptr) & 15) == 0;
+    const int64_t quads = vec ? (int64_t)c->m / 4 : (int64_t)c->m;
+    const int g = grid_capped(quads > 0 ? quads : 1, kRowStatsThreads, 4);
+    if (vec) k_rowstats<true><<<g, kRowStatsThreads, 0, s>>>(c->ptr, c->m, rs);
+    else k_rowstats<false><<<g, kRowStatsThreads, 0, s>>>(c->ptr, c->m, rs);
+    return cudaGetLastError();
 }
 
 // The cluster size for this device: 16 CTAs (a non-portable size, opted into
@@ -493,10 +641,13 @@ static int launch_features(const spmv_csr* c, float* feat, const spmv_model* mod
         return set_error(SPMV_ERR_INVALID_ARG, "malformed csr argument");
     const bool vec = (reinterpret_cast<uintptr_t>(c->idx) & 15) == 0;
     const bool large = features_ctas() == kFeatCtasLarge;
-    const cudaError_t e = large ? (vec ? launch_features_k<kFeatCtasLarge, true>(c, feat, model, fmt, logits, s)
-                                       : launch_features_k<kFeatCtasLarge, false>(c, feat, model, fmt, logits, s))
-                                : (vec ? launch_features_k<kFeatCtasSmall, true>(c, feat, model, fmt, logits, s)
-                                       : launch_features_k<kFeatCtasSmall, false>(c, feat, model, fmt, logits, s));
+    RowStatsSlot* rs = nullptr;
+    SPMV_TRY(rowstats_slot(&rs));
+    SPMV_CUDA(launch_rowstats(c, rs, s));
+    const cudaError_t e = large ? (vec ? launch_features_k<kFeatCtasLarge, true>(c, rs, feat, model, fmt, logits, s)
+                                       : launch_features_k<kFeatCtasLarge, false>(c, rs, feat, model, fmt, logits, s))
+                                : (vec ? launch_features_k<kFeatCtasSmall, true>(c, rs, feat, model, fmt, logits, s)
+                                       : launch_features_k<kFeatCtasSmall, false>(c, rs, feat, model, fmt, logits, s));
     SPMV_CUDA(e);
     return SPMV_OK;
 }
@@ -743,6 +894,10 @@ int spmv_model_create(const float* params_host, const float* lo_host, const floa
         if (e == cudaSuccess) e = cudaMemcpy(md->hi, hi_host, sizeof(float) * 16, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) st = cuda_error(e, "spmv_model_create");
     }
+    if (st == SPMV_OK) {
+        spmv_params p{};
+        md->max_bytes = resolve_cap(p);  // 90% of the memory free now
+    }
     if (st != SPMV_OK) {
         dev_free(md->params);
         dev_free(md->lo);
@@ -751,6 +906,12 @@ int spmv_model_create(const float* params_host, const float* lo_host, const floa
         return st;
     }
     *out = md;
+    return SPMV_OK;
+}
+
+int spmv_model_set_max_bytes(spmv_model* md, int64_t max_bytes) {
+    if (!md || max_bytes <= 0) return set_error(SPMV_ERR_INVALID_ARG, "model is NULL or max_bytes <= 0");
+    md->max_bytes = max_bytes;
     return SPMV_OK;
 }
 

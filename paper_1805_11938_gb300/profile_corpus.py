@@ -30,6 +30,7 @@ row).  Such a table names its classes in each line ("classes"); the shipped
 selectors keep the five formats.
 
     python -m paper_1805_11938_gb300.profile_corpus --out table.jsonl [--count 1000] [--classes 7]
+    python -m paper_1805_11938_gb300.profile_corpus --refeaturize table.jsonl --out new.jsonl
 """
 from __future__ import annotations
 
@@ -165,14 +166,45 @@ def run(out: str, count: int = 1000, start: int = 0, cap_bytes: int = FORMAT_CAP
                     f"batch best={rec['best_batch']} ({time.time() - t_start:.0f} s)", flush=True)
 
 
+def refeaturize(table: str, out: str, log=print) -> None:
+    """Rewrites a profiled table with the features the library computes now
+    (spmv_features on each regenerated matrix); the timings and labels stay."""
+    import concurrent.futures as cf2
+
+    import synth
+    from . import DeviceCSR, spmv_features
+
+    with open(table) as fh:
+        recs = [json.loads(line) for line in fh if line.strip()]
+    t0 = time.time()
+    with cf2.ThreadPoolExecutor(2) as ex, open(out + ".tmp", "w") as fo:
+        futs = {}
+        for j, r in enumerate(recs[:2]):
+            futs[j] = ex.submit(synth.corpus_matrix, r["index"])
+        for j, r in enumerate(recs):
+            a = futs.pop(j).result()
+            if j + 2 < len(recs):
+                futs[j + 2] = ex.submit(synth.corpus_matrix, recs[j + 2]["index"])
+            r["features"] = spmv_features(DeviceCSR.from_host(a)).cpu().numpy().astype(float).tolist()
+            fo.write(json.dumps(r) + "\n")
+            if j % 200 == 0:
+                log(f"[{j + 1}/{len(recs)}] ({time.time() - t0:.0f} s)", flush=True)
+    os.replace(out + ".tmp", out)
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--refeaturize", default=None, metavar="TABLE",
+                    help="rewrite TABLE's features with the current spmv_features into --out (timings kept)")
     ap.add_argument("--out", required=True)
     ap.add_argument("--count", type=int, default=1000)
     ap.add_argument("--start", type=int, default=0)
     ap.add_argument("--cap-gb", type=float, default=24.0)
     ap.add_argument("--classes", type=int, default=5, choices=(5, 7))
     args = ap.parse_args()
+    if args.refeaturize:
+        refeaturize(args.refeaturize, args.out)
+        return
     run(args.out, args.count, args.start, int(args.cap_gb * (1 << 30)),
         classes=CLASSES_7 if args.classes == 7 else CLASSES_5)
 

@@ -188,7 +188,7 @@ def main():
     ev_train = summary(recs, tr, predict(model, recs, tr), args.key)
     ev_test = summary(recs, te, predict(model, recs, te), args.key)
     out = {"params": model["params"].tolist(), "lo": model["lo"].tolist(), "hi": model["hi"].tolist(),
-           "features": "spmv_features v2 (16 features, 8192 rows sampled above 8192)",
+           "features": "spmv_features v3 (16 features; row-length statistics exact, histogram and index spread from 8192 rows sampled above 8192)",
            "timing": args.key, "cross_validation": cv,
            "training": {k: model[k] for k in ("steps", "lr", "seed", "loss_first", "loss_last")},
            "n_train": len(tr), "n_test": len(te), "train": ev_train, "held_out": ev_test}

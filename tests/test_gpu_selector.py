@@ -23,6 +23,21 @@ def _lib():
     sp = m
 
 
+def _long_row_missed(m=40_000, long_len=5000):
+    """Rows of one entry and one row of long_len entries at row 1, which the
+    8192-row sample (rows floor(k*M/8192)) skips."""
+    lens = np.ones(m, np.int32)
+    lens[1] = long_len
+    return synth.from_lengths_random_cols(lens, 7000, 13, "long_row_missed")
+
+
+def _sampled_long_rest_empty(m=40_000):
+    sampled = np.unique((np.arange(8192, dtype=np.int64) * m) // 8192)
+    lens = np.zeros(m, np.int32)
+    lens[sampled] = 40
+    return synth.from_lengths_random_cols(lens, 100, 14, "sampled_long_rest_empty")
+
+
 def _feature_cases():
     lens = np.array([0, 0, 700, 0, 3, 0, 0, 70, 1, 0] * 50, np.int32)
     return [
@@ -37,10 +52,13 @@ def _feature_cases():
         synth.uniform_random(40_000, 600, 10),            # every row longer than the 512 cap
         synth.from_lengths_random_cols(np.zeros(50, np.int32), 10, 11, "all_empty"),  # nnz = 0, idx NULL
         synth.from_lengths_random_cols(np.zeros(20_000, np.int32), 10, 12, "all_empty_sampled"),
+        _long_row_missed(),                               # exact max sees a row the sample skips
+        _sampled_long_rest_empty(),                       # exact statistics differ from the sample's
+        synth.powerlaw(2_000_003, 15, xmax=5000, lmax=5000),  # M not a multiple of 4: the scalar tail of the pass
     ]
 
 
-@pytest.mark.parametrize("ci", range(11))
+@pytest.mark.parametrize("ci", range(14))
 def test_features_match_oracle(ci):
     a = _feature_cases()[ci]
     f = sp.spmv_features(sp.DeviceCSR.from_host(a)).cpu().numpy()
@@ -185,3 +203,57 @@ def test_committed_model_on_corpus_matrices(name):
         srt = np.sort(z[0])
         if srt[-1] - srt[-2] > 1e-3:
             assert sp.spmv_select(d, model) == int(np.argmax(z[0])), i
+
+
+def test_features_exact_pass_unaligned_ptr_and_slot_reuse():
+    """The pass over ptr with ptr 4 bytes off a 16-byte boundary (the scalar
+    loads), and more calls than the ring has slots (each call finds its
+    slot's accumulators at zero again)."""
+    cases = [_long_row_missed(), _sampled_long_rest_empty(), synth.powerlaw(30_001, 16, xmax=900, lmax=900)]
+    refs = [oracle.features(a).astype(np.float32) for a in cases]
+    devs = []
+    for a in cases:
+        d = sp.DeviceCSR.from_host(a)
+        buf = torch.empty(a.m + 2, dtype=torch.int32, device="cuda")
+        buf[1:].copy_(d.ptr)
+        assert buf[1:].data_ptr() % 16 == 4
+        devs.append((d, sp.DeviceCSR(a.m, a.n, buf[1:], d.idx, d.val)))
+    for rep in range(70):
+        k = rep % len(cases)
+        d_al, d_un = devs[k]
+        for d in (d_al, d_un):
+            f = sp.spmv_features(d).cpu().numpy()
+            assert np.allclose(f, refs[k], rtol=2e-6, atol=0), (rep, cases[k].name, np.stack([f, refs[k]]))
+
+
+def _forced_model(b3):
+    """Zero weights: every logit is its bias, whatever the features."""
+    p = np.zeros(sp.MLP_PARAMS, np.float32)
+    p[5568:5573] = b3
+    return sp.Model(p, np.zeros(16, np.float32), np.ones(16, np.float32))
+
+
+def test_select_never_returns_ell_over_the_cap():
+    """A network that always prefers ELL, then SELL: on a matrix with one long
+    row the row sample misses, selection names ELL exactly while ELL's padded
+    layout fits the model's cap and SELL from one byte below it -- the same
+    footprint at which spmv_convert refuses ELL."""
+    a = _long_row_missed()
+    d = sp.DeviceCSR.from_host(a)
+    model = _forced_model([0.0, 0.0, 1.0, 0.5, 0.0])
+    ld = (a.m + 3) // 4 * 4
+    foot = ld * 5000 * 12 + ld * 4
+    model.set_max_bytes(foot)
+    assert sp.spmv_select(d, model) == sp.SPMV_ELL
+    fmt = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    logits = torch.zeros(5, dtype=torch.float32, device="cuda")
+    model.set_max_bytes(foot - 1)
+    assert sp.spmv_select(d, model) == sp.SPMV_SELL
+    sp.spmv_select_async(d, model, fmt, logits)
+    assert int(fmt.item()) == sp.SPMV_SELL and logits.cpu().numpy().tolist() == [0.0, 0.0, 1.0, 0.5, 0.0]
+    with pytest.raises(sp.SpmvError) as ei:
+        sp.spmv_convert(sp.SPMV_ELL, d, {"max_bytes": foot - 1})
+    assert ei.value.name == "TOO_LARGE"
+    assert sp.spmv_convert(sp.SPMV_ELL, d, {"max_bytes": foot}).info()["stored_slots"] == ld * 5000
+    with pytest.raises(sp.SpmvError):
+        model.set_max_bytes(0)

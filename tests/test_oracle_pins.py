@@ -416,17 +416,46 @@ def test_features_laplacian_64():
 
 
 def test_features_sampled_rows():
-    """Above 8192 rows only rows floor(k*M/8192) count: make exactly those long."""
+    """Above 8192 rows the row-length statistics stay exact over all rows,
+    while the histogram features (10, 15) and the index spread (11, 12) see only
+    rows floor(k*M/8192).  Here exactly the sampled rows are long (40 entries)
+    and every other row is empty; the values are counted by hand."""
     m = 40_000
     sampled = set((k * m) // 8192 for k in range(8192))
+    assert len(sampled) == 8192
     lens = np.array([40 if i in sampled else 0 for i in range(m)], np.int32)
     ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
     idx = np.concatenate([np.arange(40) for _ in sampled]).astype(np.int32)
     a = synth.CSR(m, 40, ptr, idx, np.ones(int(ptr[-1])))
     f = oracle.features(a)
-    assert f[3] == 40 and f[4] == 40 and f[6] == 0 and f[13] == 0 and f[14] == 1.0  # sample sees only long rows
-    assert f[5] == 40 * 8192 / m  # nnz_avg is exact, not sampled
-    assert f[10] == 0.0 and f[9] == 1.0
+    nnz = 40 * 8192
+    assert f[3] == 0 and f[4] == 40  # exact: the empty rows count
+    assert f[5] == nnz / m
+    # population std over all rows: sqrt(M * 8192 * 40^2 - nnz^2) / M
+    assert f[6] == math.sqrt(m * 8192 * 1600 - nnz * nnz) / m
+    assert f[7] == f[6] / (nnz / m) and f[9] == (nnz / m) / 40
+    assert f[13] == (m - 8192) / m and f[14] == 8192 / m
+    # the sample sees only rows of 40: K = 40, no tail; SELL-32 slices all full
+    assert f[10] == 0.0 and f[15] == 1.0
+
+
+def test_features_long_row_the_sample_misses():
+    """Rows of one entry and a single row of 5000 entries at row 1, which the
+    row sample (rows floor(k*40000/8192): 0, 4, 9, ...) skips: the exact
+    statistics see it, the sampled features do not."""
+    m = 40_000
+    assert 1 not in set((k * m) // 8192 for k in range(8192))
+    lens = np.ones(m, np.int32)
+    lens[1] = 5000
+    ptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    idx = np.concatenate([np.array([i % 7000]) if i != 1 else np.arange(5000) for i in range(m)]).astype(np.int32)
+    a = synth.CSR(m, 7000, ptr, idx, np.ones(int(ptr[-1])))
+    f = oracle.features(a)
+    nnz = m - 1 + 5000
+    assert f[4] == 5000 and f[3] == 1 and f[5] == nnz / m
+    assert f[6] == math.sqrt(m * (m - 1 + 5000 ** 2) - nnz * nnz) / m
+    assert f[9] == (nnz / m) / 5000 and f[14] == 1 / m and f[13] == 0
+    assert f[10] == 0.0 and f[15] == 1.0  # sampled: all of length 1, K = 1, full slices
 
 
 def test_features_empty_and_long():
