@@ -67,8 +67,8 @@ def make_matrix(name: str):
 def reduce_over_ranks(total_ms: float, flops: float, dist=None, device: str = "cpu") -> tuple:
     """Whole-job rate over the ranks: the slowest rank's timed total (max) and
     every rank's flops (sum); returns (max total ms, GFLOP/s).  Each rank
-    multiplies its own matrices (replicas or its share of a batch), so this is
-    the only exchange between ranks."""
+    multiplies its own row block of the one matrix (x broadcast once at setup)
+    or its own share of a batch, so the timed steps exchange nothing else."""
     if dist is not None:
         import torch
 
@@ -431,14 +431,27 @@ class Workload:
     ceiling of the matrix's index stream, and every row of the result checked
     against the oracle."""
 
-    def __init__(self, name, args, sp, torch, stream, flush, model, format_steps):
+    def __init__(self, name, args, sp, torch, stream, flush, model, format_steps, rank=0, world=1, dist=None):
         import synth
 
         self.name, self.sp, self.torch, self.stream, self.flush = name, sp, torch, stream, flush
-        self.a = a = make_matrix(name)
+        full = make_matrix(name)
+        self.total_nnz, self.total_rows = full.nnz, full.m
+        if world > 1:
+            # this rank's nnz-balanced row block of the one product (x replicated)
+            from paper_1805_11938_gb300.distributed import local_csr, row_partition
+
+            b = row_partition(full.ptr, world)
+            self.rows = (int(b[rank]), int(b[rank + 1]))
+            full = local_csr(full, *self.rows)
+        else:
+            self.rows = (0, full.m)
+        self.a = a = full
         self.xh = synth.vector(a.n, 1)
         self.d = sp.DeviceCSR.from_host(a)
         self.x = torch.as_tensor(self.xh).cuda()
+        if dist is not None:
+            dist.broadcast(self.x, 0)  # x replicated from rank 0 (the one exchange of a single product)
         self.y = torch.empty(a.m, dtype=torch.float64, device="cuda")
         self.model = model
         self.format_steps = format_steps
@@ -701,7 +714,7 @@ def main():
     stream = torch.cuda.current_stream()
     model = sp.Model.load(sp.MODEL_PATH) if os.path.exists(sp.MODEL_PATH) else None
 
-    w = Workload(args.workload, args, sp, torch, stream, flush, model, args.format_steps)
+    w = Workload(args.workload, args, sp, torch, stream, flush, model, args.format_steps, rank, world, dist)
     w.setup()
     a, x, y, xh = w.a, w.x, w.y, w.xh
 
@@ -770,8 +783,10 @@ def main():
         return t0.elapsed_time(t1) / n
 
     e2e_run(5)
+    barrier()
     e2e_ms = e2e_run(n_e2e)
     torch.cuda.synchronize()
+    e2e_ms, e2e_value = reduce_over_ranks(e2e_ms, 2.0 * a.nnz, dist, "cuda")
     e2e_same = bool(np.array_equal(yh_pin[(n_e2e - 1) % 2].numpy(), y.cpu().numpy()))
     agree = None
     if model is not None:
@@ -783,19 +798,22 @@ def main():
     summ = w.summary(total_ms / args.steps, kms)
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": a.m, "nnz": a.nnz,
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": a.n, "nnz": w.total_nnz,
                    "selected_format": summ["selected_format"], "exhaustive_best": summ["exhaustive_best"],
                    "selector": w.selector["kind"], "selected_params": summ["selected_params"], "tuning": w.tuning,
                    "step": "selector kernel + SpMV in the selected format, matrix and x resident in HBM",
                    "launch": ("the step's two kernels captured once as a CUDA graph, replayed every step"
                               if w.graph is not None else "the step's two kernels launched directly"),
                    "direct_launch_step_ms": eager_step_ms,
-                   "l2": "flushed: 256 MiB written before every timed step", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed: 256 MiB written before every timed step",
+                   "parallelism": ("one GPU" if world == 1 else
+                                   f"row blocks x{world}: nnz-balanced rows per rank, x broadcast from rank 0, each "
+                                   f"rank's y slice on its own GPU (rank 0 rows {w.rows[0]}..{w.rows[1]})")},
         "roofline": summ["roofline"],
-        "e2e": {"value": 2.0 * a.nnz / e2e_ms / 1e6, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * a.n,
-                "d2h_bytes_per_step": 8 * a.m, "ms_per_step": e2e_ms, "steps": n_e2e,
+        "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * a.n * world,
+                "d2h_bytes_per_step": 8 * w.total_rows, "ms_per_step": e2e_ms, "steps": n_e2e,
                 "copies": "pinned host x in and y out every step, double-buffered on two copy streams "
                           "(overlapping the neighbouring steps' compute)", "y_matches_device_run": e2e_same},
         "gpu_launches": args.steps * (1 + launches_per_run(w.chosen, w.info_c)),
@@ -806,11 +824,11 @@ def main():
         "wall_s_timed_region": t_wall,
         "check": check,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_rate(a, xh, args.cpu_seconds)
     del w
     torch.cuda.empty_cache()
-    if rank == 0 and extras:
+    if rank == 0 and world == 1 and extras:
         line["extra_workloads"] = {e: measure_extra(e, args, sp, torch, stream, flush, model) for e in extras}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -1,9 +1,9 @@
 """The multi-rank host path of bench.py, on CPU with gloo (world size 2).
 
-Each rank multiplies its own matrices (replicas, or its share of a batch) and
-the ranks exchange only their timed totals: the slowest rank's time (max) and
-the flops of all ranks (sum) give the whole-job rate.  The reference arm runs
-on rank 0 alone.
+Each rank multiplies its own row block of the one matrix (or its share of a
+batch) and the ranks exchange only their timed totals: the slowest rank's
+time (max) and the flops of all ranks (sum) give the whole-job rate.  The
+reference arm runs on rank 0 alone.
 """
 import json
 import os
