@@ -2,9 +2,12 @@
 
 Sec. V-B builds the predictor as a decision tree (scikit-learn's
 DecisionTreeClassifier: Gini impurity, grown until the leaves are pure);
-Sec. V-D compares it with other classifiers, among them Gaussian naive Bayes
-and the 1-nearest-neighbour rule.  They are written here from their
-definitions (numpy) and trained and scored exactly like the library's network:
+Sec. V-D compares it with the other classifiers of Fig. 11: Gaussian naive
+Bayes, the 1-nearest-neighbour rule, logistic regression, random forests and
+a soft-voting / majority-rule ensemble (the multilayer perceptron of that
+list is the library's own network).  They are written here from their
+definitions (numpy; scipy's L-BFGS minimiser for logistic regression) and
+trained and scored exactly like the library's network:
 the same 16 features after the same transform, the same 800/200 split, the
 same measure (performance of the predicted format relative to the
 exhaustively best one, Sec. V-C).  The network remains the selector the
@@ -37,16 +40,17 @@ def _gini(counts: np.ndarray) -> np.ndarray:
     return 1.0 - (p * p).sum(axis=-1)
 
 
-def best_split(X: np.ndarray, y: np.ndarray, n_classes: int = N_CLASSES):
+def best_split(X: np.ndarray, y: np.ndarray, n_classes: int = N_CLASSES, features=None):
     """The split (feature j, threshold t: left = x_j <= t) that minimises the
     sample-weighted Gini impurity of the two children, by exhaustive search
-    over every feature and every boundary between distinct sorted values;
-    the threshold is the midpoint of the two values.  Ties go to the lower
-    feature index, then the lower threshold.  None if no split separates."""
+    over every feature (or the given ones, in the given order) and every
+    boundary between distinct sorted values; the threshold is the midpoint of
+    the two values.  Ties go to the earlier feature, then the lower threshold.
+    None if no split separates."""
     n, d = X.shape
     best = None
     onehot = np.eye(n_classes, dtype=np.float64)[y]
-    for j in range(d):
+    for j in (range(d) if features is None else features):
         order = np.argsort(X[:, j], kind="stable")
         xs = X[order, j]
         left = np.cumsum(onehot[order], axis=0)[:-1]  # counts of the first i+1 samples
@@ -65,46 +69,80 @@ def best_split(X: np.ndarray, y: np.ndarray, n_classes: int = N_CLASSES):
 
 class DecisionTree:
     """CART classifier: grows until every leaf is pure or cannot be split
-    (scikit-learn's defaults), optionally bounded by max_depth."""
+    (scikit-learn's defaults), optionally bounded by max_depth.  With
+    max_features (random forests) each node draws the features to search in
+    a random order from `rng` and stops once it has searched max_features of
+    them and found a split (scikit-learn's rule: it searches on past
+    max_features while no split has been found)."""
 
-    def __init__(self, max_depth: int | None = None, n_classes: int = N_CLASSES):
+    def __init__(self, max_depth: int | None = None, n_classes: int = N_CLASSES, max_features: int | None = None,
+                 rng=None):
         self.max_depth = max_depth
         self.n_classes = n_classes
+        self.max_features = max_features
+        self.rng = rng
         self.nodes = []  # (feature, threshold, left, right, label); feature -1 for a leaf
+        self.leaf_counts = {}  # leaf node -> class counts of its training samples
 
     def fit(self, X: np.ndarray, y: np.ndarray) -> "DecisionTree":
         X = np.asarray(X, dtype=np.float64)
         y = np.asarray(y, dtype=np.int64)
         self.nodes = []
+        self.leaf_counts = {}
         self._grow(X, y, 0)
         return self
+
+    def _split(self, X, y):
+        d = X.shape[1]
+        if self.max_features is None or self.max_features >= d:
+            return best_split(X, y, self.n_classes)
+        order = self.rng.permutation(d)
+        best = None
+        for q in range(d):
+            sp = best_split(X, y, self.n_classes, features=[int(order[q])])
+            if sp is not None and (best is None or sp[2] < best[2] - 1e-15):
+                best = sp
+            if q + 1 >= self.max_features and best is not None:
+                break
+        return best
 
     def _grow(self, X, y, depth) -> int:
         counts = np.bincount(y, minlength=self.n_classes)
         label = int(np.argmax(counts))  # majority, ties to the lower class id
         k = len(self.nodes)
         self.nodes.append((-1, 0.0, -1, -1, label))
+        self.leaf_counts[k] = counts
         if counts.max() == len(y) or (self.max_depth is not None and depth >= self.max_depth):
             return k
-        sp = best_split(X, y, self.n_classes)
+        sp = self._split(X, y)
         if sp is None or sp[2] >= _gini(counts.astype(np.float64)) - 1e-15:
             return k
         j, t, _ = sp
+        del self.leaf_counts[k]
         m = X[:, j] <= t
         left = self._grow(X[m], y[m], depth + 1)
         right = self._grow(X[~m], y[~m], depth + 1)
         self.nodes[k] = (j, t, left, right, label)
         return k
 
+    def _leaf(self, x) -> int:
+        k = 0
+        while self.nodes[k][0] >= 0:
+            j, t, left, right, _ = self.nodes[k]
+            k = left if x[j] <= t else right
+        return k
+
     def predict(self, X: np.ndarray) -> np.ndarray:
         X = np.asarray(X, dtype=np.float64)
-        out = np.empty(len(X), dtype=np.int64)
+        return np.array([self.nodes[self._leaf(x)][4] for x in X], dtype=np.int64)
+
+    def predict_proba(self, X: np.ndarray) -> np.ndarray:
+        """Class fractions of the training samples in each sample's leaf."""
+        X = np.asarray(X, dtype=np.float64)
+        out = np.empty((len(X), self.n_classes))
         for i, x in enumerate(X):
-            k = 0
-            while self.nodes[k][0] >= 0:
-                j, t, left, right, _ = self.nodes[k]
-                k = left if x[j] <= t else right
-            out[i] = self.nodes[k][4]
+            c = self.leaf_counts[self._leaf(x)].astype(np.float64)
+            out[i] = c / c.sum()
         return out
 
     def depth(self) -> int:
@@ -144,6 +182,14 @@ class GaussianNB:
     def predict(self, X) -> np.ndarray:
         return self.classes[np.argmax(self.log_posterior(X), axis=1)]
 
+    def predict_proba(self, X) -> np.ndarray:
+        """Posterior probabilities over all n_classes (0 for a class absent from training)."""
+        lp = self.log_posterior(X)
+        p = np.exp(lp - lp.max(axis=1, keepdims=True))
+        out = np.zeros((len(p), self.n_classes))
+        out[:, self.classes] = p / p.sum(axis=1, keepdims=True)
+        return out
+
 
 # -------------------------------------------------------- nearest neighbour
 
@@ -160,6 +206,117 @@ class NearestNeighbour:
         X = np.asarray(X, dtype=np.float64)
         d2 = ((X[:, None, :] - self.X[None, :, :]) ** 2).sum(axis=2)
         return self.y[np.argmin(d2, axis=1)]
+
+    def predict_proba(self, X) -> np.ndarray:
+        """The neighbour's label as a one-hot distribution."""
+        return np.eye(N_CLASSES)[self.predict(X)]
+
+
+# ------------------------------------------------------ logistic regression
+
+class LogisticRegression:
+    """Multinomial logistic regression: class scores z = X W + b, softmax
+    probabilities, minimising C * (summed cross-entropy) + ||W||^2 / 2 (the
+    intercept b unpenalised), scikit-learn's objective with its default
+    C = 1.  The exact objective and gradient go to scipy's L-BFGS-B."""
+
+    def __init__(self, C: float = 1.0, n_classes: int = N_CLASSES, tol: float = 1e-10, max_iter: int = 20000):
+        self.C, self.n_classes, self.tol, self.max_iter = C, n_classes, tol, max_iter
+
+    def _unpack(self, w, d):
+        k = self.n_classes
+        return w[:d * k].reshape(d, k), w[d * k:]
+
+    def objective(self, w, X, y):
+        """(value, gradient) of the penalised loss at the flat parameters w."""
+        n, d = X.shape
+        W, b = self._unpack(w, d)
+        z = X @ W + b
+        z = z - z.max(axis=1, keepdims=True)
+        lse = np.log(np.exp(z).sum(axis=1))
+        loss = float(lse.sum() - z[np.arange(n), y].sum())
+        p = np.exp(z - lse[:, None])
+        p[np.arange(n), y] -= 1.0
+        gW = self.C * (X.T @ p) + W
+        gb = self.C * p.sum(axis=0)
+        return self.C * loss + 0.5 * float((W * W).sum()), np.concatenate([gW.ravel(), gb])
+
+    def fit(self, X, y) -> "LogisticRegression":
+        from scipy.optimize import minimize
+
+        X = np.asarray(X, dtype=np.float64)
+        y = np.asarray(y, dtype=np.int64)
+        d = X.shape[1]
+        w0 = np.zeros(d * self.n_classes + self.n_classes)
+        r = minimize(self.objective, w0, args=(X, y), jac=True, method="L-BFGS-B",
+                     options={"maxiter": self.max_iter, "gtol": self.tol, "ftol": 0.0})
+        self.W, self.b = self._unpack(r.x, d)
+        self.converged = bool(r.success)
+        return self
+
+    def predict_proba(self, X) -> np.ndarray:
+        z = np.asarray(X, dtype=np.float64) @ self.W + self.b
+        z = z - z.max(axis=1, keepdims=True)
+        e = np.exp(z)
+        return e / e.sum(axis=1, keepdims=True)
+
+    def predict(self, X) -> np.ndarray:
+        return np.argmax(self.predict_proba(X), axis=1)
+
+
+# ----------------------------------------------------------- random forests
+
+class RandomForest:
+    """Random forests: n_trees CART trees, each grown fully on a bootstrap
+    sample (n draws with replacement) with max_features = floor(sqrt(d))
+    features searched per node; the forest predicts the class of the largest
+    mean leaf-class fraction over the trees (scikit-learn's rule, ties to the
+    lower class id).  Seeded: the same seed grows the same forest."""
+
+    def __init__(self, n_trees: int = 100, max_features: int | None = None, bootstrap: bool = True, seed: int = 0,
+                 n_classes: int = N_CLASSES):
+        self.n_trees, self.max_features, self.bootstrap = n_trees, max_features, bootstrap
+        self.seed, self.n_classes = seed, n_classes
+
+    def fit(self, X, y) -> "RandomForest":
+        X = np.asarray(X, dtype=np.float64)
+        y = np.asarray(y, dtype=np.int64)
+        n, d = X.shape
+        mf = self.max_features if self.max_features is not None else max(1, int(np.sqrt(d)))
+        rng = np.random.default_rng(self.seed)
+        self.trees = []
+        for _ in range(self.n_trees):
+            rows = rng.integers(0, n, size=n) if self.bootstrap else np.arange(n)
+            t = DecisionTree(n_classes=self.n_classes, max_features=mf, rng=rng).fit(X[rows], y[rows])
+            self.trees.append(t)
+        return self
+
+    def predict_proba(self, X) -> np.ndarray:
+        return np.mean([t.predict_proba(X) for t in self.trees], axis=0)
+
+    def predict(self, X) -> np.ndarray:
+        return np.argmax(self.predict_proba(X), axis=1)
+
+
+# ------------------------------------------------------------------- voting
+
+class Voting:
+    """An ensemble of fitted classifiers.  "soft": the class of the largest
+    mean predicted probability; "hard" (majority rule): the class most of
+    them predict, ties to the lower class id."""
+
+    def __init__(self, members: list, voting: str = "soft", n_classes: int = N_CLASSES):
+        if voting not in ("soft", "hard"):
+            raise ValueError("voting is 'soft' or 'hard'")
+        self.members, self.voting, self.n_classes = members, voting, n_classes
+
+    def predict(self, Xs) -> np.ndarray:
+        """Xs: one input matrix per member (members may see differently scaled features)."""
+        if self.voting == "soft":
+            return np.argmax(np.mean([m.predict_proba(X) for m, X in zip(self.members, Xs)], axis=0), axis=1)
+        votes = np.stack([m.predict(X) for m, X in zip(self.members, Xs)], axis=1)
+        counts = np.stack([(votes == c).sum(axis=1) for c in range(self.n_classes)], axis=1)
+        return np.argmax(counts, axis=1)
 
 
 # --------------------------------------------------------------- evaluation
@@ -183,11 +340,23 @@ def compare(records, key: str = "ms") -> dict:
     def scaled(Z):
         return np.clip((Z - lo) / span, 0.0, 1.0)
 
-    models = {"DTC (the paper's)": DecisionTree().fit(Xtr, ytr), "GNB": GaussianNB().fit(Xtr, ytr),
-              "KNC (k=1)": NearestNeighbour().fit(scaled(Xtr), ytr)}
+    dtc = DecisionTree().fit(Xtr, ytr)
+    gnb = GaussianNB().fit(Xtr, ytr)
+    knc = NearestNeighbour().fit(scaled(Xtr), ytr)
+    lr = LogisticRegression().fit(scaled(Xtr), ytr)
+    rfc = RandomForest(seed=0).fit(Xtr, ytr)
+    members = [dtc, gnb, knc, lr, rfc]
+    Xs = [Xte, Xte, scaled(Xte), scaled(Xte), Xte]  # each member's own inputs
+    preds = {name: m.predict(X) for name, m, X in zip(("DTC (the paper's)", "GNB", "KNC (k=1)", "LR", "RFC"), members, Xs)}
+    # the ensemble of the five: soft voting averages the tree's leaf
+    # fractions, GNB's posterior, the neighbour's one-hot vote, LR's and the
+    # forest's probabilities; majority rule counts their predictions
+    preds["VC (soft)"] = Voting(members, "soft").predict(Xs)
+    preds["VC (majority)"] = Voting(members, "hard").predict(Xs)
     out = {}
-    for name, mdl in models.items():
-        pred = mdl.predict(scaled(Xte) if name.startswith("KNC") else Xte)
+    models = {"DTC (the paper's)": dtc}
+    for name, pred in preds.items():
+        mdl = models.get(name)
         r = pct_of_best(records, te, pred, key)
         out[name] = {"mean_pct_of_best": 100 * float(r.mean()), "worst_pct_of_best": 100 * float(r.min()),
                      "accuracy": float(np.mean(pred == np.array([records[i][LABEL_OF[key]] for i in te])))}

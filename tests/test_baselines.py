@@ -83,6 +83,86 @@ def test_nearest_neighbour_matches_sklearn_and_brute_force():
     assert np.array_equal(ours, nbrs.KNeighborsClassifier(n_neighbors=1).fit(X, y).predict(Xt))
 
 
+def test_logistic_regression_gradient_and_sklearn():
+    """The objective's gradient against central differences, and the fitted
+    model against scikit-learn's multinomial L2 logistic regression (C = 1,
+    solved to tight tolerance): the same predictions and coefficients."""
+    X, y = _data(13, n=200, d=4)
+    lr = bl.LogisticRegression()
+    w = np.random.default_rng(14).normal(size=4 * 5 + 5) * 0.3
+    f0, g = lr.objective(w, X, y)
+    h = 1e-6
+    for j in range(w.size):
+        e = np.zeros_like(w)
+        e[j] = h
+        fd = (lr.objective(w + e, X, y)[0] - lr.objective(w - e, X, y)[0]) / (2 * h)
+        assert abs(fd - g[j]) <= 1e-6 * max(1.0, abs(g[j])), j
+    ours = lr.fit(X, y)
+    assert ours.converged
+    lm = pytest.importorskip("sklearn.linear_model")
+    ref = lm.LogisticRegression(C=1.0, tol=1e-12, max_iter=100000).fit(X, y)
+    Xt, _ = _data(15, n=100, d=4)
+    assert np.array_equal(ours.predict(Xt), ref.predict(Xt))
+    assert np.allclose(ours.W.T, ref.coef_, rtol=1e-4, atol=1e-5)
+    assert np.allclose(ours.b - ours.b.mean(), ref.intercept_ - ref.intercept_.mean(), rtol=1e-4, atol=1e-5)
+
+
+def test_random_forest_special_cases_and_vote():
+    """One tree, no bootstrap, every feature searched: the forest is the plain
+    tree.  A seeded forest is reproducible, each of its trees fits its own
+    bootstrap sample of distinct points, and its prediction is the argmax of
+    the trees' mean leaf fractions, recounted here by brute force."""
+    X, y = _data(16, n=150, d=6)
+    Xt, _ = _data(17, n=60, d=6)
+    single = bl.RandomForest(n_trees=1, max_features=6, bootstrap=False).fit(X, y)
+    assert np.array_equal(single.predict(Xt), bl.DecisionTree().fit(X, y).predict(Xt))
+    f1 = bl.RandomForest(n_trees=15, seed=3).fit(X, y)
+    f2 = bl.RandomForest(n_trees=15, seed=3).fit(X, y)
+    assert np.array_equal(f1.predict_proba(Xt), f2.predict_proba(Xt))
+    # the first tree's bootstrap sample is the first draw of the seeded stream;
+    # grown to pure leaves, the tree classifies that sample perfectly
+    rows = np.random.default_rng(3).integers(0, len(X), size=len(X))
+    assert np.array_equal(f1.trees[0].predict(X[rows]), y[rows])
+    assert len(set(rows.tolist())) < len(X)  # a bootstrap sample repeats rows
+    mean = np.zeros((len(Xt), 5))
+    for t in f1.trees:
+        for i, x in enumerate(Xt):
+            k = 0
+            while t.nodes[k][0] >= 0:
+                j, th, left, right, _ = t.nodes[k]
+                k = left if x[j] <= th else right
+            c = t.leaf_counts[k]
+            mean[i] += c / c.sum() / len(f1.trees)
+    assert np.array_equal(f1.predict(Xt), np.argmax(mean, axis=1))
+
+
+def test_voting_soft_and_majority_by_hand():
+    """Majority rule: the most frequent prediction, ties to the lower class id;
+    soft voting: the argmax of the mean probability; one member alone is that
+    member."""
+
+    class Fixed:
+        def __init__(self, pred, proba):
+            self.pred, self.proba = np.array(pred), np.array(proba, dtype=np.float64)
+
+        def predict(self, X):
+            return self.pred
+
+        def predict_proba(self, X):
+            return self.proba
+
+    e = np.eye(5)
+    a = Fixed([0, 1, 2, 3], [e[0], e[1], 0.6 * e[2] + 0.4 * e[4], e[3]])
+    b = Fixed([1, 1, 4, 2], [e[1], e[1], 0.45 * e[2] + 0.55 * e[4], e[2]])
+    c = Fixed([1, 3, 4, 4], [e[1], e[3], e[4], e[4]])
+    X = [None] * 3
+    assert bl.Voting([a, b, c], "hard").predict(X).tolist() == [1, 1, 4, 2]  # last: 3, 2, 4 tie -> 2
+    # soft: sample 2 mean (0.35 on class 2, 0.65 on class 4) -> 4; sample 3: classes 2, 3, 4 tie at 1/3 -> 2
+    assert bl.Voting([a, b, c], "soft").predict(X).tolist() == [1, 1, 4, 2]
+    assert bl.Voting([a], "soft").predict([None]).tolist() == [0, 1, 2, 3]
+    assert bl.Voting([b], "hard").predict([None]).tolist() == b.pred.tolist()
+
+
 def test_stored_comparison_is_reproduced():
     """The committed comparison (every classifier on the committed table, both
     label sets) is what the code computes now, and the paper's tree reaches
