@@ -281,59 +281,58 @@ def tuning_grid(fmt: int) -> list:
     return [{}]
 
 
-def run_batch(args, rank: int, world: int) -> None:
-    """512 matrices, each in the format the selector picks with autotuned parameters, multiplied by one
-    persistent launch (CUDA graph) against the same products as 512 separate launches (also a graph)."""
-    import torch
+class BatchWorkload:
+    """n_mat matrices of the batched configuration, each in the format the
+    batch selector picks (parameters from the autotuner's grid when tune),
+    multiplied by the persistent launches replayed from a CUDA graph: the
+    kernels per task family, and one launch for every task
+    (SPMV_BATCH_ONE_LAUNCH); both against the same products as n_mat separate
+    launches (also a graph)."""
 
-    import synth
-    import paper_1805_11938_gb300 as sp
-    from paper_1805_11938_gb300 import autotune
+    def __init__(self, n_mat, args, rank, tune=True):
+        import torch
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
+        import synth
+        import paper_1805_11938_gb300 as sp
+        from paper_1805_11938_gb300 import autotune
 
-        dist.init_process_group("nccl")
-    sp.lib()
-    model_path = sp.MODEL_BATCH_PATH if os.path.exists(sp.MODEL_BATCH_PATH) else sp.MODEL_PATH
-    model = sp.Model.load(model_path)
-    timer = autotune.Timer()
-    n_mat = args.batch_count
-    handles, xs, ys, infos, mats = [], [], [], [], []
-    counts = [0] * 5
-    t0 = time.perf_counter()
-    for j in range(n_mat):
-        a = synth.batch_matrix(j + rank * n_mat)
-        d = sp.DeviceCSR.from_host(a)
-        f = sp.spmv_select(d, model) if args.batch_format < 0 else args.batch_format
-        x = torch.as_tensor(synth.vector(a.n, 900 + j)).cuda()
-        y = torch.empty(a.m, dtype=torch.float64, device="cuda")
-        best = None
-        for p in tuning_grid(f):
-            h = sp.spmv_convert(f, d, p)
-            ms = timer.measure(lambda: sp.spmv_run(h, x, y), warmup=1, n_min=5, n_max=10)["ms"]
-            if best is None or ms < best[0]:
-                best = (ms, h)
-        handles.append(best[1])
-        infos.append(best[1].info())
-        xs.append(x)
-        ys.append(y)
-        counts[f] += 1
-        if j < 8:
-            mats.append((a, j))
-        del d
-    t_setup = time.perf_counter() - t0
-    total_nnz = sum(i["nnz"] for i in infos)
-    total_rows = sum(i["m"] for i in infos)
-    b = sp.Batch(handles)
-    ys2 = [torch.empty_like(y) for y in ys]
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
+        self.torch, self.sp = torch, sp
+        self.model_path = sp.MODEL_BATCH_PATH if os.path.exists(sp.MODEL_BATCH_PATH) else sp.MODEL_PATH
+        model = sp.Model.load(self.model_path)
+        timer = autotune.Timer()
+        self.handles, self.xs, self.ys, self.infos, self.mats = [], [], [], [], []
+        self.counts = [0] * 5
+        t0 = time.perf_counter()
+        for j in range(n_mat):
+            a = synth.batch_matrix(j + rank * n_mat)
+            d = sp.DeviceCSR.from_host(a)
+            f = sp.spmv_select(d, model) if args.batch_format < 0 else args.batch_format
+            x = torch.as_tensor(synth.vector(a.n, 900 + j)).cuda()
+            y = torch.empty(a.m, dtype=torch.float64, device="cuda")
+            best = None
+            for p in (tuning_grid(f) if tune else [{}]):
+                h = sp.spmv_convert(f, d, p)
+                ms = timer.measure(lambda: sp.spmv_run(h, x, y), warmup=1, n_min=5, n_max=10)["ms"] if tune else 0.0
+                if best is None or ms < best[0]:
+                    best = (ms, h)
+            self.handles.append(best[1])
+            self.infos.append(best[1].info())
+            self.xs.append(x)
+            self.ys.append(y)
+            self.counts[f] += 1
+            if j < 8:
+                self.mats.append((a, j))
+            del d
+        self.setup_s = time.perf_counter() - t0
+        self.total_nnz = sum(i["nnz"] for i in self.infos)
+        self.total_rows = sum(i["m"] for i in self.infos)
+        self.b = sp.Batch(self.handles)
+        self.b1 = sp.Batch(self.handles, one_launch=True)
+        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        self.stream = torch.cuda.current_stream()
 
-    def timed(fn, n, warm):
+    def timed(self, fn, n, warm):
+        torch, flush, stream = self.torch, self.flush, self.stream
         for _ in range(warm):
             flush.zero_()
             fn()
@@ -347,56 +346,89 @@ def run_batch(args, rank: int, world: int) -> None:
         torch.cuda.synchronize()
         return [s0.elapsed_time(e0) for s0, e0 in evs]
 
-    if dist:
-        dist.barrier()
-    with ClockSampler(local) as clk:
-        t_b = timed(lambda: b.run(xs, ys), args.steps, args.warmup)
-    t_s = timed(lambda: b.run_separate(xs, ys2), args.steps, args.warmup)
-    clocks = clk.summary()
-    same = all(torch.equal(u, v) for u, v in zip(ys, ys2))
-    tb = statistics.mean(t_b)
-    ts = statistics.mean(t_s)
-    total_b, value = reduce_over_ranks(sum(t_b), 2.0 * total_nnz * args.steps, dist, "cuda")
-    families = batch_families(infos)
-    launches_per_replay = len(families)
-    ab = sum(algorithmic_bytes(i["fmt"], i) for i in infos)
-    peaks = {}
-    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk):
-        with open(pk) as fh:
-            peaks = json.load(fh)
-    peak = peaks.get("hbm_gbs") or 6800.0
-    batch_traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path) and args.batch_format < 0:
-        with open(tr_path) as fh:
-            batch_traffic = json.load(fh).get(f"batch{n_mat}:{os.path.basename(model_path)}")
-    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_b / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "matrices": n_mat,
-                       "rows": total_rows, "nnz": total_nnz, "formats": dict(zip(FORMATS, counts)),
-                       "format_choice": (os.path.basename(model_path) if args.batch_format < 0 else "fixed"),
-                       "l2": "flushed: 256 MiB written before every timed step", "setup_s": t_setup,
-                       "step": "one graph replay of the persistent batched kernel over all matrices"},
-            "roofline": {"bound": "hbm", "achieved": ab / tb / 1e6, "peak": peak, "unit": "GB/s",
-                         "frac": ab / tb / 1e6 / peak, "traffic": batch_traffic,
-                         "kernel": f"persistent batched product ({launches_per_replay} family kernels per replay: "
-                                   f"{', '.join(sorted(families))}); traffic summed over them",
-                         "alg_bytes_per_launch": ab},
-            "batched_ms": tb, "separate_ms": ts, "batched_speedup_over_separate": ts / tb,
-            "separate_gflops": 2.0 * total_nnz / ts / 1e6, "bitwise_equal_to_separate": same,
-            "gpu_launches": args.steps * launches_per_replay, "clocks": clocks}
-    if rank == 0 and not args.no_cpu_baseline:
+    def compare(self, steps, warmup) -> dict:
+        """Times the three ways; y of each equals the separate products bit for bit."""
+        torch = self.torch
+        ys1 = [torch.empty_like(y) for y in self.ys]
+        ys2 = [torch.empty_like(y) for y in self.ys]
+        t_one = self.timed(lambda: self.b1.run(self.xs, ys1), steps, warmup)
+        t_sep = self.timed(lambda: self.b.run_separate(self.xs, ys2), steps, warmup)
+        t_fam = self.timed(lambda: self.b.run(self.xs, self.ys), steps, warmup)
+        same = all(torch.equal(u, v) and torch.equal(u, w) for u, v, w in zip(self.ys, ys1, ys2))
+        ab = sum(algorithmic_bytes(i["fmt"], i) for i in self.infos)
+        tf, t1, ts = statistics.mean(t_fam), statistics.mean(t_one), statistics.mean(t_sep)
+        return {"matrices": len(self.handles), "rows": self.total_rows, "nnz": self.total_nnz,
+                "formats": dict(zip(FORMATS, self.counts)), "format_choice": os.path.basename(self.model_path),
+                "family_kernels_ms": tf, "family_launches": self.b.launches(),
+                "one_launch_ms": t1, "one_launch_launches": self.b1.launches(), "separate_ms": ts,
+                "speedup_families_over_separate": ts / tf, "speedup_one_launch_over_separate": ts / t1,
+                "faster": "family kernels" if tf <= t1 else "one launch",
+                "gflops_families": 2.0 * self.total_nnz / tf / 1e6, "gflops_one_launch": 2.0 * self.total_nnz / t1 / 1e6,
+                "alg_bytes": ab, "alg_gbs_best": ab / min(tf, t1) / 1e6, "bitwise_equal_all_three": same,
+                "setup_s": self.setup_s, "t_fam": t_fam, "t_one": t_one}
+
+    def check(self) -> bool:
         import oracle
 
         oks = []
-        for a, j in mats:
-            yv = ys[j].cpu().numpy()
-            xv = xs[j].cpu().numpy()
+        for a, j in self.mats:
+            yv = self.ys[j].cpu().numpy()
+            xv = self.xs[j].cpu().numpy()
             oks.append(bool(np.all(np.abs(yv - oracle.csr_spmv(a, xv)) <= oracle.fp_bound(a, xv))))
-        line["check"] = {"first_8_matrices_within_bound": all(oks)}
-        line["cpu_baseline"] = cpu_oracle_rate(mats[0][0], xs[0].cpu().numpy(), min(args.cpu_seconds, 5.0))
+        return all(oks)
+
+
+def run_batch(args, rank: int, world: int) -> None:
+    """The batched configuration: each rank multiplies its own share of
+    batch_count matrices (weak scaling).  The headline is the faster of the
+    two persistent ways, per replay."""
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    import paper_1805_11938_gb300 as sp
+
+    sp.lib()
+    bw = BatchWorkload(args.batch_count, args, rank)
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        cmp = bw.compare(args.steps, args.warmup)
+    clocks = clk.summary()
+    t_fam, t_one = cmp.pop("t_fam"), cmp.pop("t_one")
+    t_b = t_fam if cmp["faster"] == "family kernels" else t_one  # the headline: the faster way
+    tb = statistics.mean(t_b)
+    total_b, value = reduce_over_ranks(sum(t_b), 2.0 * bw.total_nnz * args.steps, dist, "cuda")
+    launches_per_replay = bw.b.launches() if cmp["faster"] == "family kernels" else bw.b1.launches()
+    peak, src = load_peaks()
+    batch_traffic = None
+    if args.batch_format < 0:
+        batch_traffic = load_traffic(f"batch{args.batch_count}:{os.path.basename(bw.model_path)}")
+    families = batch_families(bw.infos)
+    ab = cmp["alg_bytes"]
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_b / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "matrices": args.batch_count,
+                       "rows": bw.total_rows, "nnz": bw.total_nnz, "formats": dict(zip(FORMATS, bw.counts)),
+                       "format_choice": (os.path.basename(bw.model_path) if args.batch_format < 0 else "fixed"),
+                       "l2": "flushed: 256 MiB written before every timed step", "setup_s": bw.setup_s,
+                       "step": f"one graph replay of the persistent batched launches ({cmp['faster']})"},
+            "roofline": {"bound": "hbm", "achieved": ab / tb / 1e6, "peak": peak, "unit": "GB/s",
+                         "frac": ab / tb / 1e6 / peak, "traffic": batch_traffic,
+                         "kernel": f"persistent batched product ({launches_per_replay} kernels per replay; family "
+                                   f"kernels present: {', '.join(sorted(families))}); traffic summed over them",
+                         "alg_bytes_per_launch": ab, "peak_source": f"{src} hbm_gbs"},
+            "batch": cmp, "gpu_launches": args.steps * launches_per_replay, "clocks": clocks}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["check"] = {"first_8_matrices_within_bound": bw.check()}
+        a0, j0 = bw.mats[0]
+        line["cpu_baseline"] = cpu_oracle_rate(a0, bw.xs[j0].cpu().numpy(), min(args.cpu_seconds, 5.0))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -673,6 +705,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--formats", default="0,1,2,3,4")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-extra", type=int, default=32,
+                    help="after the headline: the first N matrices of the batched configuration as an extra key (0: none)")
     ap.add_argument("--batch-format", type=int, default=-1, help="batch512: one format for every matrix (-1: selector)")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps directly instead of replaying a CUDA graph")
     args = ap.parse_args()
@@ -830,6 +864,17 @@ def main():
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and extras:
         line["extra_workloads"] = {e: measure_extra(e, args, sp, torch, stream, flush, model) for e in extras}
+    if rank == 0 and world == 1 and args.batch_extra > 0:
+        bw = BatchWorkload(args.batch_extra, args, 0, tune=False)
+        cmp = bw.compare(max(10, min(args.steps, 100)), 3)
+        cmp.pop("t_fam")
+        cmp.pop("t_one")
+        cmp["check_first_8_within_bound"] = bw.check()
+        cmp["what"] = (f"the first {args.batch_extra} matrices of the batched configuration, formats from the batch "
+                       f"selector with default parameters: the family kernels, the one-launch kernel and "
+                       f"{args.batch_extra} separate launches, each replayed from a CUDA graph, L2 flushed")
+        line.setdefault("extra_workloads", {})[f"batch{args.batch_extra}"] = cmp
+        del bw
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -263,6 +263,20 @@ SPMV_API int spmv_mlp_forward(const float* theta_dev, const float* X_dev, int32_
  * (INVALID_ARG): its panels must run one after another.  Synchronises. */
 SPMV_API int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t stream, spmv_batch** out);
 
+/* spmv_batch_build with options.  flags: 0 (the kernels per task family
+ * above) or SPMV_BATCH_ONE_LAUNCH: one persistent kernel for every task but
+ * the HYB tails (which still follow in a launch of their own when present),
+ * with the largest family's register budget; SELL tasks pick their slice
+ * height at run time and CSR tile tasks share the launch's shared memory.
+ * The same products, bit for bit.  Unknown flags: INVALID_ARG. */
+#define SPMV_BATCH_ONE_LAUNCH 1
+SPMV_API int spmv_batch_build_ex(spmv_handle* const* handles, int32_t count, int32_t flags, cudaStream_t stream,
+                                 spmv_batch** out);
+
+/* Kernels one spmv_batch_run replays (the task families present, or one
+ * plus the HYB tails' under SPMV_BATCH_ONE_LAUNCH). */
+SPMV_API int spmv_batch_launches(const spmv_batch* b, int32_t* out);
+
 /* xs_host[b] / ys_host[b]: device pointers of x_b and y_b (host arrays of
  * `count` pointers).  Uploads them when they differ from the previous call,
  * then replays the graph.  Asynchronous. */

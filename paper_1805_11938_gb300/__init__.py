@@ -277,12 +277,20 @@ def spmv_mlp_forward(theta, X, stream=None):
 class Batch:
     """Several handles multiplied in one persistent launch replayed from a CUDA graph."""
 
-    def __init__(self, handles, stream=None):
+    def __init__(self, handles, stream=None, one_launch: bool = False):
         self.handles = list(handles)
         arr = (ctypes.c_void_p * len(self.handles))(*[h.raw.value for h in self.handles])
         out = ctypes.c_void_p()
-        check(lib().spmv_batch_build(arr, len(self.handles), _stream(stream), ctypes.byref(out)), "spmv_batch_build")
+        flags = _abi.SPMV_BATCH_ONE_LAUNCH if one_launch else 0
+        check(lib().spmv_batch_build_ex(arr, len(self.handles), flags, _stream(stream), ctypes.byref(out)),
+              "spmv_batch_build_ex")
         self._b = out
+
+    def launches(self) -> int:
+        """Kernels one replay runs."""
+        n = ctypes.c_int32()
+        check(lib().spmv_batch_launches(self._b, ctypes.byref(n)), "spmv_batch_launches")
+        return n.value
 
     def __del__(self):
         if getattr(self, "_b", None) and self._b.value and _abi._lib is not None:
@@ -304,8 +312,8 @@ class Batch:
         check(lib().spmv_batch_run_separate(self._b, xa, ya, _stream(stream)), "spmv_batch_run_separate")
 
 
-def spmv_batch_build(handles, stream=None) -> Batch:
-    return Batch(handles, stream)
+def spmv_batch_build(handles, stream=None, one_launch: bool = False) -> Batch:
+    return Batch(handles, stream, one_launch)
 
 
 def spmv_batch_run(b: Batch, xs, ys, stream=None):

@@ -19,6 +19,7 @@ NUM_FEATURES = 16
 MLP_PARAMS = 5573
 SPMV_HYB_K_NONE = -1
 SPMV_SELL_SIGMA_ALL = -1
+SPMV_BATCH_ONE_LAUNCH = 1
 
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "INDEX_OVERFLOW", -3: "TOO_LARGE", -4: "CUDA", -5: "NO_MODEL",
           -6: "ALLOC", -7: "WRONG_FORMAT"}
@@ -77,6 +78,8 @@ _SIGS = {
     "spmv_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I32, _I32, _I32, _F, _F, _F, _F, _VP, _VP]),
     "spmv_mlp_forward": (ctypes.c_int, [_VP, _VP, _I32, _VP, _VP, _VP]),
     "spmv_batch_build": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _VP, ctypes.POINTER(_VP)]),
+    "spmv_batch_build_ex": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _I32, _VP, ctypes.POINTER(_VP)]),
+    "spmv_batch_launches": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
     "spmv_batch_run": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     "spmv_batch_run_separate": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), _VP]),
     "spmv_batch_free": (None, [_VP]),

@@ -162,10 +162,112 @@ __global__ void __launch_bounds__(256, FAM == F_SELL1 ? 8 : (FAM == F_SELL2 ? 5 
     }
 }
 
+constexpr int kBatchAllMinBlocks = 4;
+
+// One launch for every task of the batch but the HYB tails (SPMV_BATCH_ONE_LAUNCH):
+// blocks take tasks of 8 warp units (or 256 rows) from one counter, whatever
+// their format; SELL tasks pick their slice height at run time, CSR tile tasks
+// stage their nonzeros in the dynamic shared memory the launch then reserves.
+// The register budget is the largest family's (C = 128 SELL), MINB blocks per SM.
+template <int MINB>
+__global__ void __launch_bounds__(256, MINB) k_batch_all(BatchDev B) {
+    extern __shared__ __align__(16) unsigned char batch_smem[];
+    dev::CsrWarpSmem* S = reinterpret_cast<dev::CsrWarpSmem*>(batch_smem);
+    __shared__ double red[8];
+    __shared__ int task_sh;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) task_sh = (int)atomicAdd(B.counter, 1u);
+        __syncthreads();
+        const int ti = task_sh;
+        __syncthreads();
+        if (ti >= B.n_tasks) break;
+        const int4 t = B.tasks[ti];
+        const MatDesc& md = B.mats[t.x];
+        const double* x = B.xs[t.x];
+        double* y = B.ys[t.x];
+        switch (t.y) {
+            case T_SELL: {
+                dev::SellArgs a = md.sell;
+                a.x = x;
+                a.y = y;
+                const int32_t u = t.z * 8 + warp;
+                if (u < t.w) {
+                    if (md.sell_r == 1) dev::sell_unit<1>(a, u, lane);
+                    else if (md.sell_r == 2) dev::sell_unit<2>(a, u, lane);
+                    else dev::sell_unit<4>(a, u, lane);
+                }
+                break;
+            }
+            case T_CSR: {
+                dev::CsrArgs a = md.csr;
+                const int32_t u = t.z * 8 + warp;
+                if (u < a.ntiles) {
+                    a.x = x;
+                    a.y = y;
+                    dev::csr_tile<false>(a, u, S[warp], lane);
+                }
+                break;
+            }
+            case T_CSR_ZERO: {
+                dev::CsrArgs a = md.csr;
+                a.x = x;
+                a.y = y;
+                dev::csr_zero(a, (int64_t)t.z * 256 + threadIdx.x);
+                break;
+            }
+            case T_CSR_LANES: {
+                const dev::CsrArgs& c = md.csr;
+                const int64_t row0 = (int64_t)t.z * (256 / md.csr_lanes);
+                switch (md.csr_lanes) {
+                    case 2: dev::csr_lanes_row<2>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 2, threadIdx.x & 1); break;
+                    case 4: dev::csr_lanes_row<4>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 4, threadIdx.x & 3); break;
+                    case 8: dev::csr_lanes_row<8>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 8, threadIdx.x & 7); break;
+                    case 16: dev::csr_lanes_row<16>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 16, threadIdx.x & 15); break;
+                    default: dev::csr_lanes_row<32>(c.ptr, c.idx, c.val, x, y, c.rows, row0 + threadIdx.x / 32, threadIdx.x & 31); break;
+                }
+                break;
+            }
+            case T_CSR5: {
+                dev::Csr5Args a = md.csr5;
+                a.x = x;
+                a.y = y;
+                const int64_t tile = (int64_t)t.z * 8 + warp;
+                if (tile < a.ntiles) dev::csr5_tile(a, tile, lane);
+                break;
+            }
+            case T_CSR5_ZERO: {
+                dev::Csr5Args a = md.csr5;
+                a.x = x;
+                a.y = y;
+                dev::csr5_zero_all(a, (int64_t)t.z * 256 + threadIdx.x);
+                break;
+            }
+            case T_ELL: {
+                dev::EllArgs a = md.ell;
+                a.x = x;
+                a.y = y;
+                dev::ell_rows2(a, t.z * 512 + threadIdx.x * 2);
+                break;
+            }
+            case T_ELL_LONG: {
+                dev::EllArgs a = md.ell;
+                a.x = x;
+                a.y = y;
+                dev::ell_long_row(a, md.long_rows[t.z], red);
+                break;
+            }
+            default: break;
+        }
+    }
+}
+
 }  // namespace spmv
 
 struct spmv_batch {
     int32_t count = 0;
+    int32_t flags = 0;
+    bool csr_smem = false;  // one launch: CSR tile tasks present, the launch reserves their shared memory
     std::vector<spmv_handle*> handles;
     spmv::MatDesc* d_mats = nullptr;
     int4* d_tasks[spmv::F_COUNT] = {};  // one work list per task family
@@ -263,7 +365,12 @@ static int capture_batch(spmv_batch* bt) {
         BatchDev a{bt->d_mats, bt->d_tasks[i], bt->n_tasks[i], bt->d_counters + i, bt->d_xs, bt->d_ys};
         const int grid = bt->grid[i];
         switch (i) {
-            case F_OTHER: k_batch<F_OTHER><<<grid, 256, 0, bt->cap>>>(a); break;
+            case F_OTHER:
+                if (bt->flags & SPMV_BATCH_ONE_LAUNCH)
+                    k_batch_all<kBatchAllMinBlocks><<<grid, 256, bt->csr_smem ? dev::kCsrSmemBytes : 0, bt->cap>>>(a);
+                else
+                    k_batch<F_OTHER><<<grid, 256, 0, bt->cap>>>(a);
+                break;
             case F_SELL1: k_batch<F_SELL1><<<grid, 256, 0, bt->cap>>>(a); break;
             case F_SELL2: k_batch<F_SELL2><<<grid, 256, 0, bt->cap>>>(a); break;
             case F_SELL4: k_batch<F_SELL4><<<grid, 256, 0, bt->cap>>>(a); break;
@@ -308,7 +415,13 @@ using namespace spmv;
 extern "C" {
 
 int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t stream, spmv_batch** out) {
+    return spmv_batch_build_ex(handles, count, 0, stream, out);
+}
+
+int spmv_batch_build_ex(spmv_handle* const* handles, int32_t count, int32_t flags, cudaStream_t stream,
+                        spmv_batch** out) {
     if (!handles || count <= 0 || !out) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    if (flags & ~SPMV_BATCH_ONE_LAUNCH) return set_error(SPMV_ERR_INVALID_ARG, "unknown batch flags 0x%x", flags);
     *out = nullptr;
     for (int32_t b = 0; b < count; ++b) {
         if (!handles[b]) return set_error(SPMV_ERR_INVALID_ARG, "handle %d is NULL", b);
@@ -318,10 +431,21 @@ int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t st
     }
     spmv_batch* bt = new spmv_batch();
     bt->count = count;
+    bt->flags = flags;
     bt->handles.assign(handles, handles + count);
     std::vector<MatDesc> mats(count);
     std::vector<int4> lists[F_COUNT];
     for (int32_t b = 0; b < count; ++b) fill_desc(handles[b], mats[b], lists, b);
+    if (flags & SPMV_BATCH_ONE_LAUNCH) {
+        // every list but the HYB tails goes to the one launch (its list: F_OTHER);
+        // CSR tile items become tasks of 8 tiles, one per warp (their index is
+        // already the group of 8)
+        bt->csr_smem = !lists[F_CSR].empty();
+        for (int i : {F_SELL1, F_SELL2, F_SELL4, F_CSR}) {
+            lists[F_OTHER].insert(lists[F_OTHER].end(), lists[i].begin(), lists[i].end());
+            lists[i].clear();
+        }
+    }
     int st = dev_malloc((void**)&bt->d_mats, sizeof(MatDesc) * count);
     for (int i = 0; i < F_COUNT; ++i) {
         bt->n_tasks[i] = (int32_t)lists[i].size();
@@ -350,9 +474,15 @@ int spmv_batch_build(spmv_handle* const* handles, int32_t count, cudaStream_t st
     const void* kernels[F_COUNT] = {(const void*)k_batch<F_OTHER>, (const void*)k_batch<F_SELL1>,
                                     (const void*)k_batch<F_SELL2>, (const void*)k_batch<F_SELL4>,
                                     (const void*)k_batch<F_CSR>, (const void*)k_batch<F_TAIL>};
+    if (flags & SPMV_BATCH_ONE_LAUNCH) {
+        kernels[F_OTHER] = (const void*)k_batch_all<kBatchAllMinBlocks>;
+        if (e == cudaSuccess && bt->csr_smem)
+            e = cudaFuncSetAttribute(k_batch_all<kBatchAllMinBlocks>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dev::kCsrSmemBytes);
+    }
     for (int i = 0; i < F_COUNT && e == cudaSuccess; ++i) {
         int per_sm = 0;
-        const size_t smem = (i == F_CSR || i == F_TAIL) ? dev::kCsrSmemBytes : 0;
+        const size_t smem = (i == F_CSR || i == F_TAIL || (i == F_OTHER && bt->csr_smem)) ? dev::kCsrSmemBytes : 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernels[i], 256, smem);
         // the counter-driven families fill the GPU once; the warp-striding CSR tiles take four waves
         bt->grid[i] = sms * (per_sm > 0 ? per_sm : 1) * ((i == F_CSR || i == F_TAIL) ? 4 : 1);
@@ -416,6 +546,14 @@ int spmv_batch_run_separate(spmv_batch* bt, const double* const* xs, double* con
         }
     }
     SPMV_CUDA(cudaGraphLaunch(bt->exec_sep, stream));
+    return SPMV_OK;
+}
+
+int spmv_batch_launches(const spmv_batch* bt, int32_t* out) {
+    if (!bt || !out) return set_error(SPMV_ERR_INVALID_ARG, "bad argument");
+    int32_t n = 0;
+    for (int i = 0; i < F_COUNT; ++i) n += bt->n_tasks[i] > 0;
+    *out = n;
     return SPMV_OK;
 }
 

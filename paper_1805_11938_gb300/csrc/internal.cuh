@@ -136,8 +136,11 @@ struct spmv_handle {
     double* sell_partial = nullptr;
     unsigned* sell_counters = nullptr;
     // SELL column panels: panel p covers columns [p*panel_cols, (p+1)*panel_cols)
-    // and is a SELL handle of its own; panel_pos[p][j] is the CSR position of
+    // and is a SELL handle of its own; all panels share the parent's row order
+    // (perm, owned by the parent), and sell_ys holds the partial sums per
+    // sorted position between panels.  panel_pos[p][j] is the CSR position of
     // its entry j (for the way back).  ptr keeps the CSR row pointers.
+    double* sell_ys = nullptr;
     int32_t panel_cols = 0;
     std::vector<spmv_handle*> panels;
     std::vector<int32_t*> panel_pos;

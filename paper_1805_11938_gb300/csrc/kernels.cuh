@@ -364,8 +364,12 @@ __device__ __forceinline__ void ell_long_row(const EllArgs& a, int32_t i, double
 // positions s*C + l*R .. + R-1, reading R values and R indices per slot with
 // vector loads (R = 2: 16 + 8 bytes, R = 4: 2 x 16 + 16 bytes).  Wide slices
 // are split into chunks of `unit_width` slots whose partial sums are added in
-// chunk order by the last chunk to finish.  y is written through perm (ADD:
-// added to, for the second and later column panels of a paneled matrix).
+// chunk order by the last chunk to finish.  The row sums go out by MODE:
+//   kSellPlain  y[perm[pos]] = sum            (one SELL matrix)
+//   kSellFirst  ys[pos] = sum                  (column panels sharing one row
+//   kSellMid    ys[pos] += sum                  order: the partial sums stay in
+//   kSellLast   y[perm[pos]] = ys[pos] + sum    sorted order, coalesced, until
+//                                               the last panel scatters them)
 struct SellArgs {
     const int2* units;
     const int64_t* slice_ptr;
@@ -379,9 +383,20 @@ struct SellArgs {
     int32_t unit_width;
     const double* x;
     double* y;
+    double* ys;           // panels: partial sums per sorted position
 };
 
-template <int R, bool ADD = false>
+enum SellOut : int { kSellPlain = 0, kSellFirst = 1, kSellMid = 2, kSellLast = 3 };
+
+template <int MODE>
+__device__ __forceinline__ void sell_put(const SellArgs& a, int64_t pos, double v) {
+    if constexpr (MODE == kSellPlain) a.y[a.perm[pos]] = v;
+    else if constexpr (MODE == kSellFirst) a.ys[pos] = v;
+    else if constexpr (MODE == kSellMid) a.ys[pos] += v;
+    else a.y[a.perm[pos]] = a.ys[pos] + v;
+}
+
+template <int R, int MODE = kSellPlain>
 __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane) {
     constexpr int C = 32 * R;
     const int2 U = a.units[u];
@@ -426,10 +441,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane
     if (U.y < 0) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (p0 + r < a.m) {
-                if (ADD) a.y[a.perm[p0 + r]] += acc[r];
-                else a.y[a.perm[p0 + r]] = acc[r];
-            }
+            if (p0 + r < a.m) sell_put<MODE>(a, p0 + r, acc[r]);
         return;
     }
     // chunk of a split slice
@@ -449,10 +461,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane
         double t = 0.0;
 #pragma unroll 8
         for (int32_t c = 0; c < nch; ++c) t += __ldcg(a.partial + (int64_t)(first + c) * C + lane * R + r);
-        if (p0 + r < a.m) {
-            if (ADD) a.y[a.perm[p0 + r]] += t;
-            else a.y[a.perm[p0 + r]] = t;
-        }
+        if (p0 + r < a.m) sell_put<MODE>(a, p0 + r, t);
     }
     __syncwarp();
     if (lane == 0) a.counters[first] = 0u;

@@ -25,6 +25,14 @@ __global__ void k_iota_keys(const int32_t* __restrict__ len, int32_t m, int32_t 
     }
 }
 
+// key[i] = maxlen - len[rows[i]]: the next key of a multi-key sort, in the
+// order the previous keys left.
+__global__ void k_gather_keys(const int32_t* __restrict__ len, const int32_t* __restrict__ rows, int32_t m,
+                              int32_t maxlen, uint32_t* __restrict__ key) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m) key[i] = (uint32_t)(maxlen - len[rows[i]]);
+}
+
 __global__ void k_bit_zero(const uint32_t* __restrict__ key, int32_t m, int bit, int32_t* __restrict__ z) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i <= m) z[i] = (i < m) ? (int32_t)(((key[i] >> bit) & 1u) ^ 1u) : 0;
@@ -101,7 +109,44 @@ __global__ void k_sell_scatter(const int32_t* __restrict__ ptr, const int32_t* _
     }
 }
 
-static int sell_build(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
+// Sorts rows stably, descending, within windows of sigma rows by the keys
+// lens[0..nk) taken lexicographically (lens[0] first): one-bit LSD passes
+// (a scan and a scatter each), least significant key first.  perm[pos] = row.
+static int sort_rows(const int32_t* const* lens, const int32_t* maxlens, int nk, int32_t m, int64_t sigma,
+                     int32_t* perm, cudaStream_t s, Scratch& tmp) {
+    uint32_t *key = nullptr, *key2 = nullptr;
+    int32_t *row2 = nullptr, *Z = nullptr;
+    SPMV_TRY(tmp.get(&key, (size_t)m));
+    SPMV_TRY(tmp.get(&key2, (size_t)m));
+    SPMV_TRY(tmp.get(&row2, (size_t)m));
+    SPMV_TRY(tmp.get(&Z, (size_t)m + 2));
+    k_iota_keys<<<grid_for(m, 256), 256, 0, s>>>(lens[nk - 1], m, maxlens[nk - 1], key, perm);
+    SPMV_CUDA(cudaGetLastError());
+    if (sigma <= 1) return SPMV_OK;
+    int32_t* rows_a = perm;
+    uint32_t* keys_a = key;
+    for (int q = nk - 1; q >= 0; --q) {
+        if (q != nk - 1) k_gather_keys<<<grid_for(m, 256), 256, 0, s>>>(lens[q], rows_a, m, maxlens[q], keys_a);
+        int bits = 0;
+        while (bits < 32 && (maxlens[q] >> bits) != 0) ++bits;
+        for (int b = 0; b < bits; ++b) {
+            k_bit_zero<<<grid_for((int64_t)m + 1, 256), 256, 0, s>>>(keys_a, m, b, Z);
+            SPMV_TRY(exclusive_scan<int32_t>(Z, Z, (int64_t)m + 1, s, tmp));
+            k_bit_scatter<<<grid_for(m, 256), 256, 0, s>>>(keys_a, rows_a, m, sigma, b, Z, key2, row2);
+            SPMV_CUDA(cudaGetLastError());
+            std::swap(keys_a, key2);
+            std::swap(rows_a, row2);
+        }
+    }
+    if (rows_a != perm)
+        SPMV_CUDA(cudaMemcpyAsync(perm, rows_a, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToDevice, s));
+    return SPMV_OK;
+}
+
+// Builds h's SELL layout from CSR c.  perm_in, when given, is the row order
+// to use instead of sorting c's rows (the order column panels share, owned by
+// the caller).
+static int sell_build(spmv_handle* h, const spmv_csr* c, cudaStream_t s, int32_t* perm_in = nullptr) {
     const int32_t m = c->m;
     int32_t C = h->params.sell_C ? h->params.sell_C : 32;
     if (C != 32 && C != 64 && C != 128) return set_error(SPMV_ERR_INVALID_ARG, "sell_C must be 32, 64 or 128 (got %d)", C);
@@ -115,38 +160,18 @@ static int sell_build(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     h->sell_C = C;
     h->sell_sigma = (int32_t)sigma;
     Scratch tmp;
-    int32_t *len = nullptr, *Z = nullptr, *ipos = nullptr;
-    uint32_t *key = nullptr, *key2 = nullptr;
-    int32_t* row2 = nullptr;
+    int32_t *len = nullptr, *ipos = nullptr;
     SPMV_TRY(tmp.get(&len, (size_t)m + 1));
     SPMV_TRY(row_lengths(c->ptr, m, len, s));
     int32_t maxlen = 0;
     SPMV_TRY(max_i32(len, m, &maxlen, s, tmp));
-    SPMV_TRY(h->alloc(&h->perm, (size_t)m, "perm"));
-    SPMV_TRY(tmp.get(&key, (size_t)m));
-    SPMV_TRY(tmp.get(&key2, (size_t)m));
-    SPMV_TRY(tmp.get(&row2, (size_t)m));
-    SPMV_TRY(tmp.get(&Z, (size_t)m + 2));
     SPMV_TRY(tmp.get(&ipos, (size_t)m));
-    k_iota_keys<<<grid_for(m, 256), 256, 0, s>>>(len, m, maxlen, key, h->perm);
-    SPMV_CUDA(cudaGetLastError());
-    if (sigma > 1) {
-        int bits = 0;
-        while (bits < 32 && (maxlen >> bits) != 0) ++bits;
-        int32_t* rows_a = h->perm;
-        uint32_t* keys_a = key;
-        for (int b = 0; b < bits; ++b) {
-            k_bit_zero<<<grid_for((int64_t)m + 1, 256), 256, 0, s>>>(keys_a, m, b, Z);
-            SPMV_TRY(exclusive_scan<int32_t>(Z, Z, (int64_t)m + 1, s, tmp));
-            k_bit_scatter<<<grid_for(m, 256), 256, 0, s>>>(keys_a, rows_a, m, sigma, b, Z, key2, row2);
-            SPMV_CUDA(cudaGetLastError());
-            std::swap(keys_a, key2);
-            std::swap(rows_a, row2);
-        }
-        if (rows_a != h->perm) {
-            SPMV_CUDA(cudaMemcpyAsync(h->perm, rows_a, sizeof(int32_t) * (size_t)m, cudaMemcpyDeviceToDevice, s));
-            row2 = rows_a;
-        }
+    if (perm_in) {
+        h->perm = perm_in;
+    } else {
+        SPMV_TRY(h->alloc(&h->perm, (size_t)m, "perm"));
+        const int32_t* lens[1] = {len};
+        SPMV_TRY(sort_rows(lens, &maxlen, 1, m, sigma, h->perm, s, tmp));
     }
     const int64_t ns = ceil_div(m, C);
     const int64_t mp = ns * C;
@@ -267,29 +292,50 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     h->panel_cols = (int32_t)pc;
     if (pc >= n) return sell_build(h, c, s);
 
-    // column panels: one SELL matrix per band of pc columns
+    // column panels: one SELL matrix per band of pc columns, all in one row
+    // order -- rows sorted by their panel lengths taken lexicographically
+    // (panel 0's first), which keeps every panel's slices nearly full -- so
+    // the partial sums stay in sorted order between panels.
     const int32_t np = (int32_t)ceil_div(n, pc);
     SPMV_TRY(h->alloc(&h->ptr, (size_t)m + 1, "ptr"));
     SPMV_CUDA(cudaMemcpyAsync(h->ptr, c->ptr, sizeof(int32_t) * ((size_t)m + 1), cudaMemcpyDeviceToDevice, s));
+    Scratch keep;  // per panel: its row lengths and row pointers
+    std::vector<int32_t*> cnts(np), sub_ptrs(np);
+    std::vector<int32_t> maxl(np), nnzs(np);
+    for (int32_t p = 0; p < np; ++p) {
+        const int32_t c0 = (int32_t)(p * pc), c1 = (int32_t)std::min<int64_t>(n, (int64_t)(p + 1) * pc);
+        SPMV_TRY(keep.get(&cnts[p], (size_t)m + 1));
+        SPMV_TRY(keep.get(&sub_ptrs[p], (size_t)m + 1));
+        k_panel_count<<<grid_for((int64_t)m + 1, 256), 256, 0, s>>>(c->ptr, c->idx, m, c0, c1, cnts[p]);
+        SPMV_CUDA(cudaGetLastError());
+        Scratch tmp;
+        SPMV_TRY(exclusive_scan<int32_t>(cnts[p], sub_ptrs[p], m, s, tmp));
+        SPMV_TRY(max_i32(cnts[p], m, &maxl[p], s, tmp));
+        SPMV_CUDA(cudaMemcpyAsync(&nnzs[p], sub_ptrs[p] + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        SPMV_CUDA(cudaStreamSynchronize(s));
+    }
+    int64_t sigma = h->params.sell_sigma ? h->params.sell_sigma : (int64_t)m;
+    if (sigma == SPMV_SELL_SIGMA_ALL || sigma > m) sigma = m;
+    {
+        SPMV_TRY(h->alloc(&h->perm, (size_t)m, "perm"));
+        Scratch tmp;
+        std::vector<const int32_t*> lens(cnts.begin(), cnts.end());
+        SPMV_TRY(sort_rows(lens.data(), maxl.data(), np, m, sigma, h->perm, s, tmp));
+        SPMV_CUDA(cudaStreamSynchronize(s));
+    }
+    SPMV_TRY(h->alloc(&h->sell_ys, (size_t)m, nullptr));
     int64_t slots = 0, ns = 0, nu = 0, maxlen = 0;
     for (int32_t p = 0; p < np; ++p) {
         const int32_t c0 = (int32_t)(p * pc), c1 = (int32_t)std::min<int64_t>(n, (int64_t)(p + 1) * pc);
+        const int32_t nnz_p = nnzs[p];
         Scratch tmp;
-        int32_t *cnt = nullptr, *sub_ptr = nullptr, *sub_idx = nullptr, *pos = nullptr;
+        int32_t *sub_idx = nullptr, *pos = nullptr;
         double* sub_val = nullptr;
-        SPMV_TRY(tmp.get(&cnt, (size_t)m + 1));
-        SPMV_TRY(tmp.get(&sub_ptr, (size_t)m + 1));
-        k_panel_count<<<grid_for((int64_t)m + 1, 256), 256, 0, s>>>(c->ptr, c->idx, m, c0, c1, cnt);
-        SPMV_CUDA(cudaGetLastError());
-        SPMV_TRY(exclusive_scan<int32_t>(cnt, sub_ptr, m, s, tmp));
-        int32_t nnz_p = 0;
-        SPMV_CUDA(cudaMemcpyAsync(&nnz_p, sub_ptr + m, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        SPMV_CUDA(cudaStreamSynchronize(s));
         SPMV_TRY(tmp.get(&sub_idx, (size_t)nnz_p + 1));
         SPMV_TRY(tmp.get(&sub_val, (size_t)nnz_p + 1));
         SPMV_TRY(h->alloc(&pos, (size_t)nnz_p + 1, nullptr));
-        k_panel_scatter<<<grid_for(m, 256), 256, 0, s>>>(c->ptr, c->idx, c->val, m, c0, c1, sub_ptr, sub_idx, sub_val,
-                                                         pos);
+        k_panel_scatter<<<grid_for(m, 256), 256, 0, s>>>(c->ptr, c->idx, c->val, m, c0, c1, sub_ptrs[p], sub_idx,
+                                                         sub_val, pos);
         SPMV_CUDA(cudaGetLastError());
         spmv_handle* child = new spmv_handle();
         h->panels.push_back(child);  // owned by h from here on
@@ -301,8 +347,10 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
         child->device = h->device;
         child->params = h->params;
         child->params.sell_panel_cols = SPMV_SELL_PANELS_NONE;
-        const spmv_csr sub{m, c1 - c0, (int64_t)nnz_p, sub_ptr, sub_idx, sub_val};
-        SPMV_TRY(sell_build(child, &sub, s));
+        const spmv_csr sub{m, c1 - c0, (int64_t)nnz_p, sub_ptrs[p], sub_idx, sub_val};
+        SPMV_TRY(sell_build(child, &sub, s, h->perm));  // the shared order; the child does not own it
+        child->sell_ys = h->sell_ys;
+        SPMV_CUDA(cudaStreamSynchronize(s));
         h->device_bytes += child->device_bytes;
         slots += child->stored_slots;
         ns += child->aux[0];
@@ -325,12 +373,12 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
 // split into chunks, first, so the static split is balanced).  Register
 // budgets keep 8 / 5 / 4 blocks resident for C = 32 / 64 / 128 (measured:
 // C = 32 on the power-law matrix 77.6 us at 40 registers, 74.8 at 32).
-template <int R, bool ADD>
+template <int R, int MODE>
 __global__ void __launch_bounds__(256, R == 1 ? 8 : (R == 2 ? 5 : 4)) k_sell(dev::SellArgs a, int32_t nu) {
     dev::pdl_wait();  // launched early (launch_pdl): wait for the kernel ahead
     const int32_t stride = (int32_t)gridDim.x * 8;
     for (int32_t u = (int32_t)(blockIdx.x * 8 + (threadIdx.x >> 5)); u < nu; u += stride)
-        dev::sell_unit<R, ADD>(a, u, threadIdx.x & 31);
+        dev::sell_unit<R, MODE>(a, u, threadIdx.x & 31);
 }
 
 // Blocks of the SELL kernel: four waves of resident blocks, each warp taking
@@ -344,29 +392,29 @@ static int32_t sell_grid() {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell<R, false>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sell<R, dev::kSellPlain>, 256, 0);
         g = sms * (per_sm > 0 ? per_sm : 1) * 4;
     }
     return g;
 }
 
-template <bool ADD>
+template <int MODE>
 static void sell_launch(const spmv_handle* h, const double* x, double* y, cudaStream_t s) {
     dev::SellArgs a{h->sell_units, h->slice_ptr, h->sell_len, h->perm, h->sell_col, h->sell_val,
-                    h->sell_partial, h->sell_counters, h->m, kSellUnitWidth, x, y};
+                    h->sell_partial, h->sell_counters, h->m, kSellUnitWidth, x, y, h->sell_ys};
     if (h->n_sell_units <= 0) return;
     const int64_t need = grid_for(h->n_sell_units, 8);
     switch (h->sell_C) {
         case 32:
-            launch_pdl(k_sell<1, ADD>, dim3((unsigned)std::min<int64_t>(need, sell_grid<1>())), dim3(256), 0, s, a,
+            launch_pdl(k_sell<1, MODE>, dim3((unsigned)std::min<int64_t>(need, sell_grid<1>())), dim3(256), 0, s, a,
                        h->n_sell_units);
             break;
         case 64:
-            launch_pdl(k_sell<2, ADD>, dim3((unsigned)std::min<int64_t>(need, sell_grid<2>())), dim3(256), 0, s, a,
+            launch_pdl(k_sell<2, MODE>, dim3((unsigned)std::min<int64_t>(need, sell_grid<2>())), dim3(256), 0, s, a,
                        h->n_sell_units);
             break;
         default:
-            launch_pdl(k_sell<4, ADD>, dim3((unsigned)std::min<int64_t>(need, sell_grid<4>())), dim3(256), 0, s, a,
+            launch_pdl(k_sell<4, MODE>, dim3((unsigned)std::min<int64_t>(need, sell_grid<4>())), dim3(256), 0, s, a,
                        h->n_sell_units);
             break;
     }
@@ -374,12 +422,14 @@ static void sell_launch(const spmv_handle* h, const double* x, double* y, cudaSt
 
 int sell_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s) {
     if (h->panels.empty()) {
-        sell_launch<false>(h, x, y, s);
-    } else {  // y = A_0 x_0, then y += A_p x_p in panel order
-        for (size_t p = 0; p < h->panels.size(); ++p) {
+        sell_launch<dev::kSellPlain>(h, x, y, s);
+    } else {  // ys = A_0 x_0, ys += A_p x_p, then y = ys + A_last x_last through the shared row order
+        const size_t np = h->panels.size();
+        for (size_t p = 0; p < np; ++p) {
             const double* xp = x + (int64_t)p * h->panel_cols;
-            if (p == 0) sell_launch<false>(h->panels[p], xp, y, s);
-            else sell_launch<true>(h->panels[p], xp, y, s);
+            if (p == 0) sell_launch<dev::kSellFirst>(h->panels[p], xp, y, s);
+            else if (p + 1 < np) sell_launch<dev::kSellMid>(h->panels[p], xp, y, s);
+            else sell_launch<dev::kSellLast>(h->panels[p], xp, y, s);
         }
     }
     SPMV_CUDA(cudaGetLastError());

@@ -28,9 +28,10 @@ def _mats(n):
     return out
 
 
+@pytest.mark.parametrize("one_launch", [False, True])
 @pytest.mark.parametrize("params", [None, {"csr5_sigma": 4, "sell_C": 128, "sell_sigma": 256, "hyb_k": 2},
                                     {"csr_block_nnz": -8}, {"csr_block_nnz": 352}])
-def test_batch_matches_single_runs(sp, params):
+def test_batch_matches_single_runs(sp, params, one_launch):
     mats = _mats(23)
     handles, xs, ys, ys2, singles = [], [], [], [], []
     for j, a in enumerate(mats):
@@ -42,7 +43,10 @@ def test_batch_matches_single_runs(sp, params):
         ys.append(torch.full((a.m,), np.nan, dtype=torch.float64, device="cuda"))
         ys2.append(torch.full((a.m,), np.nan, dtype=torch.float64, device="cuda"))
         singles.append(sp.spmv_run(h, x).cpu().numpy())
-    b = sp.Batch(handles)
+    b = sp.Batch(handles, one_launch=one_launch)
+    if one_launch:  # one kernel, plus the HYB tails' own when there are any
+        tails = any(h.info()["fmt"] == 4 and h.info()["aux"][1] > 0 for h in handles)
+        assert b.launches() == 1 + tails
     for rep in range(3):  # replays reuse counters and scratch
         b.run(xs, ys)
         b.run_separate(xs, ys2)
@@ -76,3 +80,28 @@ def test_batch_refuses_sell_in_column_panels(sp):
     with pytest.raises(sp.SpmvError) as ei:
         sp.Batch([h])
     assert ei.value.name == "INVALID_ARG"
+
+
+def test_batch_one_launch_mixed_sell_heights(sp):
+    """SELL matrices of all three slice heights in one launch (the height picked
+    per task at run time): bit for bit each matrix's own product."""
+    mats = _mats(12)
+    handles = [sp.spmv_convert(3, sp.DeviceCSR.from_host(a), {"sell_C": (32, 64, 128)[j % 3]})
+               for j, a in enumerate(mats)]
+    xs = [torch.as_tensor(synth.vector(a.n, 700 + j)).cuda() for j, a in enumerate(mats)]
+    singles = [sp.spmv_run(h, x).cpu().numpy() for h, x in zip(handles, xs)]
+    b = sp.Batch(handles, one_launch=True)
+    assert b.launches() == 1
+    assert sp.Batch(handles).launches() == 3  # the family kernels: one per slice height
+    ys = [torch.full((a.m,), np.nan, dtype=torch.float64, device="cuda") for a in mats]
+    for rep in range(2):
+        b.run(xs, ys)
+        torch.cuda.synchronize()
+        for j in range(len(mats)):
+            assert np.array_equal(bits(ys[j].cpu().numpy()), bits(singles[j])), (j, rep)
+    import ctypes
+
+    arr = (ctypes.c_void_p * 1)(handles[0].raw.value)
+    out = ctypes.c_void_p()
+    assert sp.lib().spmv_batch_build_ex(arr, 1, 2, None, ctypes.byref(out)) == -1  # unknown flag
+    assert not out.value
