@@ -47,6 +47,11 @@ WORKLOADS = {
     "graph_2e7": "n = 20,000,000 power-law graph, mean about 12 entries per row, at most 1e5",
     "batch512": "512 matrices, rows log-uniform in [1e3, 2e5], row lengths in [3, 200] (half uniform, half "
                 "power-law), one persistent launch replayed from a CUDA graph",
+    # scaled-down cases of the two large configurations, for hardware-counter
+    # captures (inputs larger than L2, a few GB on the device)
+    "stencil27_112": "3D 27-point stencil on 112^3 (n = 1,404,928, nnz = 37,259,704): the 224^3 stencil scaled down",
+    "graph_1e7_lite": "1e7 rows x 2e7 columns (x 160 MB, as the 2e7 graph's), row lengths ceil(Pareto alpha 2.1) "
+                      "on [1, 1e5], uniform columns: the 2e7 graph scaled down",
 }
 
 
@@ -61,6 +66,11 @@ def make_matrix(name: str):
         return synth.config5_stencil()
     if name == "graph_2e7":
         return synth.config5_graph()
+    if name == "stencil27_112":
+        return synth.config5_stencil(112)
+    if name == "graph_1e7_lite":
+        lens = synth.powerlaw_lengths(10_000_000, synth.seed_of(5, 2), xmax=1e5, lmax=100_000)
+        return synth.from_lengths_random_cols(lens, 20_000_000, synth.seed_of(5, 2), "graph_1e7_lite")
     raise SystemExit(f"unknown workload {name}")
 
 

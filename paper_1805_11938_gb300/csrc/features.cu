@@ -180,6 +180,7 @@ constexpr int kRowSlots = 64;
 static __device__ RowStatsSlot g_rowstats[kRowSlots];
 
 constexpr int kRowStatsThreads = 256;
+constexpr int kRowStatsUnroll = 4;  // 16-byte loads in flight per thread
 
 template <bool VEC>
 __global__ void __launch_bounds__(kRowStatsThreads) k_rowstats(const int32_t* __restrict__ ptr, int32_t m,
@@ -202,19 +203,28 @@ __global__ void __launch_bounds__(kRowStatsThreads) k_rowstats(const int32_t* __
     if constexpr (VEC) {
         // quad q = rows 4q .. 4q+3 from one 16-byte load of ptr[4q .. 4q+3];
         // ptr[4q+4] is the next lane's first word (loaded directly by lane 31
-        // and by the last quad)
+        // and by the last quad).  A warp takes kRowStatsUnroll runs of 32
+        // consecutive quads at a time, all loads issued before any is used.
         const int64_t nq = (int64_t)m / 4;
-        for (int64_t qb = gt - lane; qb < nq; qb += nt) {  // warp-uniform bound
-            const int64_t q = qb + lane;
-            int4 v = make_int4(0, 0, 0, 0);
-            if (q < nq) v = __ldcs(reinterpret_cast<const int4*>(ptr) + q);
-            int32_t nx = __shfl_down_sync(dev::kFull, v.x, 1);
-            if (q < nq) {
-                if (lane == 31 || q + 1 == nq) nx = __ldcs(ptr + 4 * q + 4);
-                add(v.y - v.x);
-                add(v.z - v.y);
-                add(v.w - v.z);
-                add(nx - v.w);
+        constexpr int U = kRowStatsUnroll;
+        for (int64_t qb = (gt - lane) * U; qb < nq; qb += nt * U) {  // warp-uniform bound
+            int4 v[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int64_t q = qb + 32 * k + lane;
+                v[k] = q < nq ? __ldcs(reinterpret_cast<const int4*>(ptr) + q) : make_int4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int64_t q = qb + 32 * k + lane;
+                int32_t nx = __shfl_down_sync(dev::kFull, v[k].x, 1);
+                if (q < nq) {
+                    if (lane == 31 || q + 1 == nq) nx = __ldcs(ptr + 4 * q + 4);
+                    add(v[k].y - v[k].x);
+                    add(v[k].z - v[k].y);
+                    add(v[k].w - v[k].z);
+                    add(nx - v[k].w);
+                }
             }
         }
         tail0 = 4 * nq;
@@ -586,8 +596,8 @@ static int rowstats_slot(RowStatsSlot** out) {
 
 static cudaError_t launch_rowstats(const spmv_csr* c, RowStatsSlot* rs, cudaStream_t s) {
     const bool vec = (reinterpret_cast<uintptr_t>(c->ptr) & 15) == 0;
-    const int64_t quads = vec ? (int64_t)c->m / 4 : (int64_t)c->m;
-    const int g = grid_capped(quads > 0 ? quads : 1, kRowStatsThreads, 4);
+    const int64_t items = vec ? (int64_t)c->m / 4 / kRowStatsUnroll : (int64_t)c->m;
+    const int g = grid_capped(items > 0 ? items : 1, kRowStatsThreads, 4);
     if (vec) k_rowstats<true><<<g, kRowStatsThreads, 0, s>>>(c->ptr, c->m, rs);
     else k_rowstats<false><<<g, kRowStatsThreads, 0, s>>>(c->ptr, c->m, rs);
     return cudaGetLastError();
