@@ -388,12 +388,16 @@ struct SellArgs {
 
 enum SellOut : int { kSellPlain = 0, kSellFirst = 1, kSellMid = 2, kSellLast = 3 };
 
+// perm and the sorted-order partial sums are streamed (evict-first loads,
+// streaming stores), so that they do not push x out of L2; the scattered y
+// stores keep the default policy, so that neighbouring rows' writes can meet
+// in L2 before a sector goes to memory.
 template <int MODE>
 __device__ __forceinline__ void sell_put(const SellArgs& a, int64_t pos, double v) {
-    if constexpr (MODE == kSellPlain) a.y[a.perm[pos]] = v;
-    else if constexpr (MODE == kSellFirst) a.ys[pos] = v;
-    else if constexpr (MODE == kSellMid) a.ys[pos] += v;
-    else a.y[a.perm[pos]] = a.ys[pos] + v;
+    if constexpr (MODE == kSellPlain) a.y[__ldcs(a.perm + pos)] = v;
+    else if constexpr (MODE == kSellFirst) __stcs(a.ys + pos, v);
+    else if constexpr (MODE == kSellMid) __stcs(a.ys + pos, __ldcs(a.ys + pos) + v);
+    else a.y[__ldcs(a.perm + pos)] = __ldcs(a.ys + pos) + v;
 }
 
 template <int R, int MODE = kSellPlain>
@@ -409,7 +413,7 @@ __device__ __forceinline__ void sell_unit(const SellArgs& a, int32_t u, int lane
     double acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        L[r] = a.len[p0 + r];
+        L[r] = __ldcs(a.len + p0 + r);
         acc[r] = 0.0;
     }
     int32_t lmax = 0;

@@ -25,6 +25,15 @@ __global__ void k_iota_keys(const int32_t* __restrict__ len, int32_t m, int32_t 
     }
 }
 
+// Group of row i in the shared order of column panels, as a descending key:
+// rows longer than long_len first (group 0), then the other rows in windows
+// of `window` consecutive rows (group 1 + i / window).  g[i] = gmax - group.
+__global__ void k_panel_group(const int32_t* __restrict__ ptr, int32_t m, int32_t long_len, int64_t window,
+                              int32_t gmax, int32_t* __restrict__ g) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m) g[i] = gmax - (ptr[i + 1] - ptr[i] > long_len ? 0 : (int32_t)(1 + i / window));
+}
+
 // key[i] = maxlen - len[rows[i]]: the next key of a multi-key sort, in the
 // order the previous keys left.
 __global__ void k_gather_keys(const int32_t* __restrict__ len, const int32_t* __restrict__ rows, int32_t m,
@@ -232,6 +241,8 @@ static int sell_build(spmv_handle* h, const spmv_csr* c, cudaStream_t s, int32_t
 // (the 2e7-row power-law graph: 2.8 -> about 1.8 ms).
 constexpr int64_t kPanelAutoBytes = 96ll << 20;
 constexpr int64_t kPanelBytes = 64ll << 20;
+constexpr int32_t kPanelLongRow = 32;         // longer rows are sorted over the whole matrix
+constexpr int64_t kPanelWindow = 1ll << 18;   // the other rows, in windows of this many rows (2 MiB of y)
 
 // Entries of row i with column in [c0, c1).
 __global__ void k_panel_count(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t m, int32_t c0,
@@ -293,9 +304,14 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     if (pc >= n) return sell_build(h, c, s);
 
     // column panels: one SELL matrix per band of pc columns, all in one row
-    // order -- rows sorted by their panel lengths taken lexicographically
-    // (panel 0's first), which keeps every panel's slices nearly full -- so
-    // the partial sums stay in sorted order between panels.
+    // order, so that the partial sums stay in sorted order between panels.
+    // The order: rows longer than kPanelLongRow first, then the other rows in
+    // windows of kPanelWindow consecutive rows; inside each group, rows sorted
+    // by their panel lengths taken lexicographically (panel 0's first), which
+    // keeps every panel's slices nearly full.  The windows keep the last
+    // panel's writes of y within a window's few MiB, so that neighbouring
+    // rows meet in L2 and whole sectors go to memory (scattered over all of y,
+    // every 8-byte write costs a sector read and write).
     const int32_t np = (int32_t)ceil_div(n, pc);
     SPMV_TRY(h->alloc(&h->ptr, (size_t)m + 1, "ptr"));
     SPMV_CUDA(cudaMemcpyAsync(h->ptr, c->ptr, sizeof(int32_t) * ((size_t)m + 1), cudaMemcpyDeviceToDevice, s));
@@ -319,8 +335,18 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     {
         SPMV_TRY(h->alloc(&h->perm, (size_t)m, "perm"));
         Scratch tmp;
-        std::vector<const int32_t*> lens(cnts.begin(), cnts.end());
-        SPMV_TRY(sort_rows(lens.data(), maxl.data(), np, m, sigma, h->perm, s, tmp));
+        int32_t* grp = nullptr;
+        SPMV_TRY(tmp.get(&grp, (size_t)m));
+        const int64_t window = std::min<int64_t>(sigma, kPanelWindow);
+        const int32_t gmax = (int32_t)(1 + (m - 1) / window);
+        k_panel_group<<<grid_for(m, 256), 256, 0, s>>>(c->ptr, m, kPanelLongRow, window, gmax, grp);
+        SPMV_CUDA(cudaGetLastError());
+        std::vector<const int32_t*> lens{grp};
+        lens.insert(lens.end(), cnts.begin(), cnts.end());
+        std::vector<int32_t> maxk{gmax};
+        maxk.insert(maxk.end(), maxl.begin(), maxl.end());
+        // sigma = 1 (plain SELL) keeps the rows in order; otherwise one global sort by (group, panel lengths)
+        SPMV_TRY(sort_rows(lens.data(), maxk.data(), np + 1, m, sigma > 1 ? m : 1, h->perm, s, tmp));
         SPMV_CUDA(cudaStreamSynchronize(s));
     }
     SPMV_TRY(h->alloc(&h->sell_ys, (size_t)m, nullptr));

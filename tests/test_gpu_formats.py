@@ -123,21 +123,25 @@ def test_sell_panels_unsorted_columns_and_duplicates():
         assert np.array_equal(pt, ptr) and np.array_equal(it, idx) and np.array_equal(bits(vt), bits(val)), pc
 
 
-@pytest.mark.parametrize("pc,C", [(5000, 32), (7001, 64), (2500, 128)])
-def test_sell_panels_share_one_row_order(pc, C):
-    """Column panels keep one row order: rows sorted, stably and descending, by
-    their per-panel lengths taken lexicographically (panel 0 first), so that
-    partial sums stay in that order between panels.  The handle's perm is
-    compared with numpy's stable lexsort of the lengths counted on the host;
-    y and the way back are exact on integer-valued inputs."""
-    a = synth.with_integer_values(MATS[1], 55)  # power-law rows, 3000 columns
+@pytest.mark.parametrize("pc,C,sigma", [(5000, 32, 0), (7001, 64, 1024), (2500, 128, 128)])
+def test_sell_panels_share_one_row_order(pc, C, sigma):
+    """Column panels keep one row order, so that partial sums stay in that
+    order between panels: rows longer than 32 entries first, then the others
+    in windows of min(sigma, 2^18) consecutive rows; inside each group, rows
+    sorted, stably and descending, by their per-panel lengths taken
+    lexicographically (panel 0 first).  The handle's perm is compared with
+    numpy's stable lexsort of the keys counted on the host; y and the way back
+    are exact on integer-valued inputs."""
+    a = synth.with_integer_values(MATS[1], 55)  # power-law rows, 20000 x 20000
     x = synth.integers(a.n, 56, -7, 7)
-    h, y = _run(a, 3, {"sell_panel_cols": pc, "sell_C": C}, x)
+    h, y = _run(a, 3, {"sell_panel_cols": pc, "sell_C": C, "sell_sigma": sigma}, x)
     P = -(-a.n // pc)
     assert h.info()["aux"][3] == P
     rows = np.repeat(np.arange(a.m), np.diff(a.ptr))
     lens = [np.bincount(rows[(a.idx // pc) == p], minlength=a.m) for p in range(P)]
-    order = np.lexsort(tuple(-l for l in reversed(lens)))
+    window = min(a.m if sigma == 0 else sigma, 1 << 18)
+    group = np.where(np.diff(a.ptr) > 32, 0, 1 + np.arange(a.m) // window)
+    order = np.lexsort(tuple(-l for l in reversed(lens)) + (group,))
     assert np.array_equal(h.array("perm").cpu().numpy(), order)
     assert np.array_equal(bits(y), bits(oracle.csr_spmv(a, x)))
     pt, it, vt = (t.cpu().numpy() for t in sp.spmv_to_csr(h))
