@@ -37,6 +37,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1805_11938_gb300.autotune import L2Flush  # noqa: E402
+
 METRIC = "FP64 SpMV GFLOP/s & HBM GB/s vs ~8 TB/s; selector % of best-format throughput"
 FORMATS = ("CSR", "CSR5", "ELL", "SELL", "HYB")
 
@@ -338,18 +340,18 @@ class BatchWorkload:
         self.total_rows = sum(i["m"] for i in self.infos)
         self.b = sp.Batch(self.handles)
         self.b1 = sp.Batch(self.handles, one_launch=True)
-        self.flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        self.flush = L2Flush()
         self.stream = torch.cuda.current_stream()
 
     def timed(self, fn, n, warm):
         torch, flush, stream = self.torch, self.flush, self.stream
         for _ in range(warm):
-            flush.zero_()
+            flush()
             fn()
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         for s0, e0 in evs:
-            flush.zero_()
+            flush()
             s0.record(stream)
             fn()
             e0.record(stream)
@@ -427,7 +429,7 @@ def run_batch(args, rank: int, world: int) -> None:
             "config": {"workload": "batch512", "description": WORKLOADS["batch512"], "matrices": args.batch_count,
                        "rows": bw.total_rows, "nnz": bw.total_nnz, "formats": dict(zip(FORMATS, bw.counts)),
                        "format_choice": (os.path.basename(bw.model_path) if args.batch_format < 0 else "fixed"),
-                       "l2": "flushed: 256 MiB written before every timed step", "setup_s": bw.setup_s,
+                       "l2": bw.flush.describe(), "setup_s": bw.setup_s,
                        "step": f"one graph replay of the persistent batched launches ({cmp['faster']})"},
             "roofline": {"bound": "hbm", "achieved": ab / tb / 1e6, "peak": peak, "unit": "GB/s",
                          "frac": ab / tb / 1e6 / peak, "traffic": batch_traffic,
@@ -502,12 +504,12 @@ class Workload:
     def timed(self, fn, n, warm):
         torch, flush, stream = self.torch, self.flush, self.stream
         for _ in range(warm):
-            flush.zero_()
+            flush()
             fn()
         torch.cuda.synchronize()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         for s, e in evs:
-            flush.zero_()
+            flush()
             s.record(stream)
             fn()
             e.record(stream)
@@ -615,7 +617,7 @@ class Workload:
         """Warm-up, then the step's two launches captured once as a CUDA graph."""
         torch = self.torch
         for _ in range(warmup):
-            self.flush.zero_()
+            self.flush()
             self.step()
         torch.cuda.synchronize()
         self.graph = None
@@ -625,7 +627,7 @@ class Workload:
                 self.step()
             torch.cuda.synchronize()
             for _ in range(warmup):
-                self.flush.zero_()
+                self.flush()
                 self.graph.replay()
         return self.graph.replay if self.graph is not None else self.step
 
@@ -638,7 +640,7 @@ class Workload:
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
                torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         for s, mid, e in ev:
-            self.flush.zero_()
+            self.flush()
             s.record(stream)
             self.select_step()
             mid.record(stream)
@@ -754,7 +756,7 @@ def main():
     import paper_1805_11938_gb300 as sp
 
     sp.lib()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = L2Flush()
     stream = torch.cuda.current_stream()
     model = sp.Model.load(sp.MODEL_PATH) if os.path.exists(sp.MODEL_PATH) else None
 
@@ -773,7 +775,7 @@ def main():
         barrier()
         t_wall = time.perf_counter()
         for s, e in ev:
-            flush.zero_()
+            flush()
             s.record(stream)
             run_step()
             e.record(stream)
@@ -784,6 +786,13 @@ def main():
     clocks = clk.summary()
     kern_ms, eager_step_ms = w.kernel_pass(args.steps)
     check = w.check_all_rows() if rank == 0 else None
+    # the same steps after a write-only flush (its dirty lines then go back to
+    # memory during the step), for comparison with the headline's flush
+    dirty = L2Flush(clean=False)
+    w.flush = dirty
+    dirty_ms = statistics.mean(w.timed(run_step, max(20, min(args.steps, 200)), 3))
+    w.flush = flush
+    del dirty
 
     # ---- end to end: every step copies its x in from pinned host memory, runs
     # the step through the library, and copies its y out.  x and y are
@@ -851,7 +860,8 @@ def main():
                    "launch": ("the step's two kernels captured once as a CUDA graph, replayed every step"
                               if w.graph is not None else "the step's two kernels launched directly"),
                    "direct_launch_step_ms": eager_step_ms,
-                   "l2": "flushed: 256 MiB written before every timed step",
+                   "step_ms_after_write_only_flush": dirty_ms,
+                   "l2": flush.describe(),
                    "parallelism": ("one GPU" if world == 1 else
                                    f"row blocks x{world}: nnz-balanced rows per rank, x broadcast from rank 0, each "
                                    f"rank's y slice on its own GPU (rank 0 rows {w.rows[0]}..{w.rows[1]})")},

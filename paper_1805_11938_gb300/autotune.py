@@ -26,20 +26,47 @@ def _t95(n: int) -> float:
     return T95.get(n, 1.96 + 2.5 / max(n - 1, 1))
 
 
+class L2Flush:
+    """Evicts L2 between timed runs.  Writes a buffer larger than L2, so that
+    nothing a timed kernel touched stays cached, then (clean=True) reads a
+    second such buffer, so that the dirty lines of that write are written
+    back to memory before the next timed run starts rather than during it
+    (where they would add up to L2's size of writes to the kernel's time)."""
+
+    def __init__(self, nbytes: int = 256 << 20, clean: bool = True):
+        import torch
+
+        self.w = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self.r = torch.zeros(nbytes // 8, dtype=torch.int64, device="cuda") if clean else None
+        self.out = torch.zeros((), dtype=torch.int64, device="cuda")
+        self.torch = torch
+
+    def __call__(self):
+        self.w.zero_()
+        if self.r is not None:
+            self.torch.sum(self.r, dim=0, out=self.out)
+
+    def describe(self) -> str:
+        mib = self.w.numel() >> 20
+        return (f"flushed: {mib} MiB written, then {mib} MiB read, before every timed step (the write evicts the "
+                f"last step's data, the read writes the flush's dirty lines back before the step)"
+                if self.r is not None else f"flushed: {mib} MiB written before every timed step")
+
+
 class Timer:
-    """CUDA-event timing of one callable, L2 flushed before each run."""
+    """CUDA-event timing of one callable, L2 flushed (L2Flush) before each run."""
 
     def __init__(self, flush_bytes: int = 256 << 20):
         import torch
 
         self.torch = torch
-        self.flush = torch.empty(flush_bytes, dtype=torch.uint8, device="cuda")
+        self.flush = L2Flush(flush_bytes)
         self.stream = torch.cuda.current_stream()
 
     def once(self, fn) -> float:
         t = self.torch
         s, e = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
-        self.flush.zero_()
+        self.flush()
         s.record(self.stream)
         fn()
         e.record(self.stream)
@@ -50,7 +77,7 @@ class Timer:
         t = self.torch
         evs = [(t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)) for _ in range(n)]
         for s, e in evs:
-            self.flush.zero_()
+            self.flush()
             s.record(self.stream)
             fn()
             e.record(self.stream)

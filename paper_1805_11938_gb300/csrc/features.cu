@@ -180,7 +180,7 @@ constexpr int kRowSlots = 64;
 static __device__ RowStatsSlot g_rowstats[kRowSlots];
 
 constexpr int kRowStatsThreads = 256;
-constexpr int kRowStatsUnroll = 4;  // 16-byte loads in flight per thread
+constexpr int kRowStatsUnroll = 8;  // 16-byte loads in flight per thread
 
 template <bool VEC>
 __global__ void __launch_bounds__(kRowStatsThreads) k_rowstats(const int32_t* __restrict__ ptr, int32_t m,
