@@ -271,7 +271,8 @@ def run_reference(args, rank: int, world: int) -> None:
     sample = (f"{args.steps} row blocks of about {REF_BLOCK_NNZ} nonzeros ({flops // 2} nonzeros in all) of the "
               f"{a.m}-row matrix, C, rows split over {cores} threads")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak" if args.workload == "batch512" else "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": WORKLOADS[args.workload], "n": a.m, "nnz": a.nnz,
                        "step": "CPU oracle product of one row block (about 2^22 nonzeros)"},
