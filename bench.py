@@ -302,7 +302,7 @@ class BatchWorkload:
     (SPMV_BATCH_ONE_LAUNCH); both against the same products as n_mat separate
     launches (also a graph)."""
 
-    def __init__(self, n_mat, args, rank, tune=True):
+    def __init__(self, n_mat, args, rank, tune=True, mixed=False):
         import torch
 
         import synth
@@ -319,7 +319,10 @@ class BatchWorkload:
         for j in range(n_mat):
             a = synth.batch_matrix(j + rank * n_mat)
             d = sp.DeviceCSR.from_host(a)
-            f = sp.spmv_select(d, model) if args.batch_format < 0 else args.batch_format
+            if mixed:  # every format in turn
+                f = j % 5
+            else:
+                f = sp.spmv_select(d, model) if args.batch_format < 0 else args.batch_format
             x = torch.as_tensor(synth.vector(a.n, 900 + j)).cuda()
             y = torch.empty(a.m, dtype=torch.float64, device="cuda")
             best = None
@@ -895,6 +898,15 @@ def main():
                        f"selector with default parameters: the family kernels, the one-launch kernel and "
                        f"{args.batch_extra} separate launches, each replayed from a CUDA graph, L2 flushed")
         line.setdefault("extra_workloads", {})[f"batch{args.batch_extra}"] = cmp
+        del bw
+        bw = BatchWorkload(args.batch_extra, args, 0, tune=False, mixed=True)
+        cmp = bw.compare(max(10, min(args.steps, 100)), 3)
+        cmp.pop("t_fam")
+        cmp.pop("t_one")
+        cmp["check_first_8_within_bound"] = bw.check()
+        cmp["what"] = (f"the same {args.batch_extra} matrices, matrix j in format j mod 5 (CSR, CSR5, ELL, SELL, HYB) "
+                       f"with default parameters: family kernels against the one-launch kernel on a mixed batch")
+        line["extra_workloads"][f"batch{args.batch_extra}_mixed"] = cmp
         del bw
     if rank == 0:
         print(json.dumps(line), flush=True)
