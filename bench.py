@@ -110,6 +110,11 @@ def algorithmic_bytes(fmt: int, info: dict) -> int:
     return base + 4 * m + 8 * aux[1] + 8 * aux[1]
 
 
+# kernels of one selection (include/spmv.h, spmv_select_async): the exact pass
+# over ptr and the features cluster
+SELECT_LAUNCHES = 2
+
+
 def launches_per_run(fmt: int, info: dict) -> int:
     """Kernels one spmv_run launches (include/spmv.h, spmv_run)."""
     aux = info["aux"]
@@ -874,7 +879,7 @@ def main():
                 "d2h_bytes_per_step": 8 * w.total_rows, "ms_per_step": e2e_ms, "steps": n_e2e,
                 "copies": "pinned host x in and y out every step, double-buffered on two copy streams "
                           "(overlapping the neighbouring steps' compute)", "y_matches_device_run": e2e_same},
-        "gpu_launches": args.steps * (1 + launches_per_run(w.chosen, w.info_c)),
+        "gpu_launches": args.steps * (SELECT_LAUNCHES + launches_per_run(w.chosen, w.info_c)),
         "clocks": clocks,
         "formats": w.per_fmt,
         "selector": dict(w.selector, per_step_agrees=agree),
