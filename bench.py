@@ -76,6 +76,15 @@ def make_matrix(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def dist_backend() -> tuple:
+    """The process group's backend and the device its tensors live on: NCCL
+    between GPUs; SPMV_BENCH_BACKEND=gloo runs the same ranks' exchanges on the
+    host (for checking the multi-rank path where only one GPU is at hand --
+    the ranks' kernels never wait on one another)."""
+    b = os.environ.get("SPMV_BENCH_BACKEND", "nccl")
+    return b, ("cuda" if b == "nccl" else "cpu")
+
+
 def reduce_over_ranks(total_ms: float, flops: float, dist=None, device: str = "cpu") -> tuple:
     """Whole-job rate over the ranks: the slowest rank's timed total (max) and
     every rank's flops (sum); returns (max total ms, GFLOP/s).  Each rank
@@ -405,13 +414,13 @@ def run_batch(args, rank: int, world: int) -> None:
     two persistent ways, per replay."""
     import torch
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0")) % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl")
+        dist.init_process_group(dist_backend()[0])
     import paper_1805_11938_gb300 as sp
 
     sp.lib()
@@ -424,7 +433,7 @@ def run_batch(args, rank: int, world: int) -> None:
     t_fam, t_one = cmp.pop("t_fam"), cmp.pop("t_one")
     t_b = t_fam if cmp["faster"] == "family kernels" else t_one  # the headline: the faster way
     tb = statistics.mean(t_b)
-    total_b, value = reduce_over_ranks(sum(t_b), 2.0 * bw.total_nnz * args.steps, dist, "cuda")
+    total_b, value = reduce_over_ranks(sum(t_b), 2.0 * bw.total_nnz * args.steps, dist, dist_backend()[1])
     launches_per_replay = bw.b.launches() if cmp["faster"] == "family kernels" else bw.b1.launches()
     peak, src = load_peaks()
     batch_traffic = None
@@ -503,8 +512,13 @@ class Workload:
         self.xh = synth.vector(a.n, 1)
         self.d = sp.DeviceCSR.from_host(a)
         self.x = torch.as_tensor(self.xh).cuda()
-        if dist is not None:
-            dist.broadcast(self.x, 0)  # x replicated from rank 0 (the one exchange of a single product)
+        if dist is not None:  # x replicated from rank 0 (the one exchange of a single product)
+            if dist_backend()[1] == "cuda":
+                dist.broadcast(self.x, 0)
+            else:
+                xc = self.x.cpu()
+                dist.broadcast(xc, 0)
+                self.x.copy_(xc)
         self.y = torch.empty(a.m, dtype=torch.float64, device="cuda")
         self.model = model
         self.format_steps = format_steps
@@ -749,13 +763,13 @@ def main():
 
     import torch
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0")) % max(1, torch.cuda.device_count())
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl")
+        dist.init_process_group(dist_backend()[0])
 
     def barrier():
         if dist:
@@ -791,7 +805,7 @@ def main():
         barrier()
         t_wall = time.perf_counter() - t_wall
     step_ms = [s.elapsed_time(e) for s, e in ev]
-    total_ms, value = reduce_over_ranks(sum(step_ms), 2.0 * a.nnz * args.steps, dist, "cuda")
+    total_ms, value = reduce_over_ranks(sum(step_ms), 2.0 * a.nnz * args.steps, dist, dist_backend()[1])
     clocks = clk.summary()
     kern_ms, eager_step_ms = w.kernel_pass(args.steps)
     check = w.check_all_rows() if rank == 0 else None
@@ -848,7 +862,7 @@ def main():
     barrier()
     e2e_ms = e2e_run(n_e2e)
     torch.cuda.synchronize()
-    e2e_ms, e2e_value = reduce_over_ranks(e2e_ms, 2.0 * a.nnz, dist, "cuda")
+    e2e_ms, e2e_value = reduce_over_ranks(e2e_ms, 2.0 * a.nnz, dist, dist_backend()[1])
     e2e_same = bool(np.array_equal(yh_pin[(n_e2e - 1) % 2].numpy(), y.cpu().numpy()))
     agree = None
     if model is not None:
