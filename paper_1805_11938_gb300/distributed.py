@@ -67,8 +67,11 @@ class RowPartitioned:
     """This rank's row block of A and the exchange steps around its product."""
 
     def __init__(self, a, rank: int, world: int, dist=None, multiply=None, fmt: int | None = None,
-                 params: dict | None = None, model=None):
+                 params: dict | None = None, model=None, device: str | None = None):
         self.rank, self.world, self.dist = rank, world, dist
+        # where this rank's y lives (and, for a rank without rows, the buffer
+        # it contributes to the gather): the GPU for the library's product
+        self.device = device or ("cuda" if multiply is None else "cpu")
         self.bounds = row_partition(a.ptr, world)
         self.r0, self.r1 = int(self.bounds[rank]), int(self.bounds[rank + 1])
         self.block = local_csr(a, self.r0, self.r1)
@@ -102,7 +105,7 @@ class RowPartitioned:
         from . import spmv_run
 
         if self.block.m == 0:
-            return y_block
+            return y_block if y_block is not None else x.new_empty(0)
         return spmv_run(self.handle, x, y_block, stream)
 
     def gather_y(self, y_block):
@@ -114,7 +117,7 @@ class RowPartitioned:
             return y_block
         sizes = np.diff(self.bounds)
         width = int(sizes.max())
-        buf = torch.zeros(width, dtype=torch.float64, device=y_block.device if y_block is not None else "cpu")
+        buf = torch.zeros(width, dtype=torch.float64, device=y_block.device if y_block is not None else self.device)
         if self.rows:
             buf[:self.rows] = y_block
         parts = [torch.empty_like(buf) for _ in range(self.world)]

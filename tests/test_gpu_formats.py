@@ -123,7 +123,7 @@ def test_sell_panels_unsorted_columns_and_duplicates():
         assert np.array_equal(pt, ptr) and np.array_equal(it, idx) and np.array_equal(bits(vt), bits(val)), pc
 
 
-@pytest.mark.parametrize("pc,C,sigma", [(5000, 32, 0), (7001, 64, 1024), (2500, 128, 128)])
+@pytest.mark.parametrize("pc,C,sigma", [(5000, 32, 0), (7001, 64, 1024), (2500, 128, 128), (5000, 32, 1)])
 def test_sell_panels_share_one_row_order(pc, C, sigma):
     """Column panels keep one row order, so that partial sums stay in that
     order between panels: rows longer than 32 entries first, then the others
@@ -142,6 +142,8 @@ def test_sell_panels_share_one_row_order(pc, C, sigma):
     window = min(a.m if sigma == 0 else sigma, 1 << 18)
     group = np.where(np.diff(a.ptr) > 32, 0, 1 + np.arange(a.m) // window)
     order = np.lexsort(tuple(-l for l in reversed(lens)) + (group,))
+    if sigma == 1:  # plain SELL: no sorting at all
+        order = np.arange(a.m)
     assert np.array_equal(h.array("perm").cpu().numpy(), order)
     assert np.array_equal(bits(y), bits(oracle.csr_spmv(a, x)))
     pt, it, vt = (t.cpu().numpy() for t in sp.spmv_to_csr(h))
