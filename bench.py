@@ -454,7 +454,7 @@ def run_batch(args, rank: int, world: int) -> None:
                          "kernel": f"persistent batched product ({launches_per_replay} kernels per replay; family "
                                    f"kernels present: {', '.join(sorted(families))}); traffic summed over them",
                          "alg_bytes_per_launch": ab, "peak_source": f"{src} hbm_gbs"},
-            "batch": cmp, "gpu_launches": args.steps * launches_per_replay, "clocks": clocks}
+            "batch": cmp, "gpu_launches": world * args.steps * launches_per_replay, "clocks": clocks}
     if rank == 0 and not args.no_cpu_baseline:
         line["check"] = {"first_8_matrices_within_bound": bw.check()}
         a0, j0 = bw.mats[0]
@@ -893,7 +893,7 @@ def main():
                 "d2h_bytes_per_step": 8 * w.total_rows, "ms_per_step": e2e_ms, "steps": n_e2e,
                 "copies": "pinned host x in and y out every step, double-buffered on two copy streams "
                           "(overlapping the neighbouring steps' compute)", "y_matches_device_run": e2e_same},
-        "gpu_launches": args.steps * (SELECT_LAUNCHES + launches_per_run(w.chosen, w.info_c)),
+        "gpu_launches": world * args.steps * (SELECT_LAUNCHES + launches_per_run(w.chosen, w.info_c)),
         "clocks": clocks,
         "formats": w.per_fmt,
         "selector": dict(w.selector, per_step_agrees=agree),

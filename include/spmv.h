@@ -95,7 +95,7 @@ typedef struct {
                               is split by columns into panels, each a SELL matrix of its own, and
                               y = sum over panels of A_p x_p (in panel order), so that each panel's
                               part of x stays in L2.  The panels share one row order (rows longer
-                              than 32 entries first, then windows of min(sell_sigma, 2^18) rows,
+                              than 32 entries first, then windows of min(sell_sigma, 2^16) rows,
                               each sorted by the rows' panel lengths), so the partial sums stay in
                               that order and only the last panel writes y.  > 0 explicit,
                               SPMV_SELL_PANELS_NONE -> one panel, 0 -> panels of at most 64 MiB of

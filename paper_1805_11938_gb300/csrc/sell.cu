@@ -242,7 +242,7 @@ static int sell_build(spmv_handle* h, const spmv_csr* c, cudaStream_t s, int32_t
 constexpr int64_t kPanelAutoBytes = 96ll << 20;
 constexpr int64_t kPanelBytes = 64ll << 20;
 constexpr int32_t kPanelLongRow = 32;         // longer rows are sorted over the whole matrix
-constexpr int64_t kPanelWindow = 1ll << 18;   // the other rows, in windows of this many rows (2 MiB of y)
+constexpr int64_t kPanelWindow = 1ll << 16;   // the other rows, in windows of this many rows (512 KiB of y)
 
 // Entries of row i with column in [c0, c1).
 __global__ void k_panel_count(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t m, int32_t c0,

@@ -127,7 +127,7 @@ def test_sell_panels_unsorted_columns_and_duplicates():
 def test_sell_panels_share_one_row_order(pc, C, sigma):
     """Column panels keep one row order, so that partial sums stay in that
     order between panels: rows longer than 32 entries first, then the others
-    in windows of min(sigma, 2^18) consecutive rows; inside each group, rows
+    in windows of min(sigma, 2^16) consecutive rows; inside each group, rows
     sorted, stably and descending, by their per-panel lengths taken
     lexicographically (panel 0 first).  The handle's perm is compared with
     numpy's stable lexsort of the keys counted on the host; y and the way back
@@ -139,7 +139,7 @@ def test_sell_panels_share_one_row_order(pc, C, sigma):
     assert h.info()["aux"][3] == P
     rows = np.repeat(np.arange(a.m), np.diff(a.ptr))
     lens = [np.bincount(rows[(a.idx // pc) == p], minlength=a.m) for p in range(P)]
-    window = min(a.m if sigma == 0 else sigma, 1 << 18)
+    window = min(a.m if sigma == 0 else sigma, 1 << 16)
     group = np.where(np.diff(a.ptr) > 32, 0, 1 + np.arange(a.m) // window)
     order = np.lexsort(tuple(-l for l in reversed(lens)) + (group,))
     if sigma == 1:  # plain SELL: no sorting at all
