@@ -97,9 +97,9 @@ typedef struct {
                               part of x stays in L2.  The panels share one row order (rows longer
                               than 32 entries first, then windows of min(sell_sigma, 2^16) rows,
                               each sorted by the rows' panel lengths), so the partial sums stay in
-                              that order and only the last panel writes y.  > 0 explicit,
-                              SPMV_SELL_PANELS_NONE -> one panel, 0 -> panels of at most 64 MiB of
-                              x when x exceeds 96 MiB */
+                              that order and only the last panel writes y.  > 0 explicit (at most
+                              256 panels, else INVALID_ARG), SPMV_SELL_PANELS_NONE -> one panel,
+                              0 -> panels of at most 64 MiB of x when x exceeds 96 MiB */
     int64_t max_bytes;     /* cap on the handle's device footprint (0 -> 90% of free memory) */
 } spmv_params;
 

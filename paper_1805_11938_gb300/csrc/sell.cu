@@ -243,6 +243,7 @@ constexpr int64_t kPanelAutoBytes = 96ll << 20;
 constexpr int64_t kPanelBytes = 64ll << 20;
 constexpr int32_t kPanelLongRow = 32;         // longer rows are sorted over the whole matrix
 constexpr int64_t kPanelWindow = 1ll << 16;   // the other rows, in windows of this many rows (512 KiB of y)
+constexpr int kPanelMax = 256;                // panels are sort keys of the shared order: a bounded number
 
 // Entries of row i with column in [c0, c1).
 __global__ void k_panel_count(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t m, int32_t c0,
@@ -312,7 +313,11 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     // panel's writes of y within a window's few MiB, so that neighbouring
     // rows meet in L2 and whole sectors go to memory (scattered over all of y,
     // every 8-byte write costs a sector read and write).
-    const int32_t np = (int32_t)ceil_div(n, pc);
+    const int64_t np64 = ceil_div(n, pc);
+    if (np64 > kPanelMax)
+        return set_error(SPMV_ERR_INVALID_ARG, "%lld column panels requested; at most %d (sell_panel_cols >= %lld)",
+                         (long long)np64, kPanelMax, (long long)ceil_div(n, kPanelMax));
+    const int32_t np = (int32_t)np64;
     SPMV_TRY(h->alloc(&h->ptr, (size_t)m + 1, "ptr"));
     SPMV_CUDA(cudaMemcpyAsync(h->ptr, c->ptr, sizeof(int32_t) * ((size_t)m + 1), cudaMemcpyDeviceToDevice, s));
     Scratch keep;  // per panel: its row lengths and row pointers

@@ -150,6 +150,21 @@ def test_sell_panels_share_one_row_order(pc, C, sigma):
     assert np.array_equal(pt, a.ptr) and np.array_equal(it, a.idx) and np.array_equal(bits(vt), bits(a.val))
 
 
+def test_sell_panel_count_is_bounded():
+    """Panels are keys of the shared row order's sort, so their number is
+    bounded: 300 panels are refused (INVALID_ARG), 200 convert and multiply."""
+    lens = np.full(500, 4, np.int32)
+    a = synth.with_integer_values(synth.from_lengths_random_cols(lens, 600, 19, "narrow"), 20)
+    d = sp.DeviceCSR.from_host(a)
+    with pytest.raises(sp.SpmvError) as ei:
+        sp.spmv_convert(sp.SPMV_SELL, d, {"sell_panel_cols": 2})
+    assert ei.value.name == "INVALID_ARG"
+    x = synth.integers(a.n, 21, -5, 5)
+    h, y = _run(a, 3, {"sell_panel_cols": 3}, x)
+    assert h.info()["aux"][3] == 200
+    assert np.array_equal(bits(y), bits(oracle.csr_spmv(a, x)))
+
+
 def test_sell_panel_rule_splits_large_x():
     """x of 13e6 doubles (99 MiB, above 96 MiB) is split into panels of at most
     64 MiB of x; a smaller x stays in one panel."""
