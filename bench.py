@@ -129,8 +129,8 @@ def launches_per_run(fmt: int, info: dict) -> int:
     aux = info["aux"]
     if fmt == 1:
         return 1 if (aux[0] > 0 or aux[2] > 0) else 0
-    if fmt == 3:  # one launch per column panel
-        return max(1, aux[3])
+    if fmt == 3:  # one launch per column panel and one putting y back in row order
+        return aux[3] + 1 if aux[3] > 0 else 1
     if fmt == 4:
         return 1 + (1 if aux[1] > 0 else 0)
     return 1

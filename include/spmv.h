@@ -97,7 +97,7 @@ typedef struct {
                               part of x stays in L2.  The panels share one row order (rows longer
                               than 32 entries first, then windows of min(sell_sigma, 2^16) rows,
                               each sorted by the rows' panel lengths), so the partial sums stay in
-                              that order and only the last panel writes y.  > 0 explicit (at most
+                              that order; a last pass writes y in row order.  > 0 explicit (at most
                               256 panels, else INVALID_ARG), SPMV_SELL_PANELS_NONE -> one panel,
                               0 -> panels of at most 64 MiB of x when x exceeds 96 MiB */
     int64_t max_bytes;     /* cap on the handle's device footprint (0 -> 90% of free memory) */
@@ -151,7 +151,8 @@ SPMV_API int spmv_convert(spmv_fmt fmt, const spmv_csr* csr, const spmv_params* 
  * doubles, both device memory.  Asynchronous on `stream`; no host sync, no
  * allocation (the call can be captured into a CUDA graph).  Launches the
  * format's kernels: one (CSR, CSR5, ELL, SELL), two (HYB with a COO tail),
- * or one per column panel (SELL in panels, in panel order).  They are
+ * or one per column panel, in panel order, and one putting y in row order
+ * (SELL in panels).  They are
  * launched with programmatic stream serialization: their blocks may become
  * resident while the kernel ahead of them in `stream` finishes, and each
  * waits for that kernel to complete (its writes visible) before it touches

@@ -180,10 +180,10 @@ constexpr int kRowSlots = 64;
 static __device__ RowStatsSlot g_rowstats[kRowSlots];
 
 constexpr int kRowStatsThreads = 256;
-constexpr int kRowStatsUnroll = 8;  // 16-byte loads in flight per thread
+constexpr int kRowStatsUnroll = 4;  // 16-byte loads in flight per thread
 
 template <bool VEC>
-__global__ void __launch_bounds__(kRowStatsThreads) k_rowstats(const int32_t* __restrict__ ptr, int32_t m,
+__global__ void __launch_bounds__(kRowStatsThreads, 6) k_rowstats(const int32_t* __restrict__ ptr, int32_t m,
                                                                RowStatsSlot* __restrict__ slot) {
     dev::pdl_trigger();  // the features kernel behind this one may start now
     unsigned mx = 0, cmn = 0, emp = 0, lng = 0;
@@ -597,7 +597,7 @@ static int rowstats_slot(RowStatsSlot** out) {
 static cudaError_t launch_rowstats(const spmv_csr* c, RowStatsSlot* rs, cudaStream_t s) {
     const bool vec = (reinterpret_cast<uintptr_t>(c->ptr) & 15) == 0;
     const int64_t items = vec ? (int64_t)c->m / 4 / kRowStatsUnroll : (int64_t)c->m;
-    const int g = grid_capped(items > 0 ? items : 1, kRowStatsThreads, 4);
+    const int g = grid_capped(items > 0 ? items : 1, kRowStatsThreads, 6);
     if (vec) k_rowstats<true><<<g, kRowStatsThreads, 0, s>>>(c->ptr, c->m, rs);
     else k_rowstats<false><<<g, kRowStatsThreads, 0, s>>>(c->ptr, c->m, rs);
     return cudaGetLastError();

@@ -138,9 +138,11 @@ struct spmv_handle {
     // SELL column panels: panel p covers columns [p*panel_cols, (p+1)*panel_cols)
     // and is a SELL handle of its own; all panels share the parent's row order
     // (perm, owned by the parent), and sell_ys holds the partial sums per
-    // sorted position between panels.  panel_pos[p][j] is the CSR position of
+    // sorted position between panels; after the last panel, y[i] =
+    // sell_ys[sell_ipos[i]] (rows in order, whole sectors written).  panel_pos[p][j] is the CSR position of
     // its entry j (for the way back).  ptr keeps the CSR row pointers.
     double* sell_ys = nullptr;
+    int32_t* sell_ipos = nullptr;  // panels: row -> sorted position (the inverse of perm)
     int32_t panel_cols = 0;
     std::vector<spmv_handle*> panels;
     std::vector<int32_t*> panel_pos;

@@ -365,11 +365,11 @@ __device__ __forceinline__ void ell_long_row(const EllArgs& a, int32_t i, double
 // vector loads (R = 2: 16 + 8 bytes, R = 4: 2 x 16 + 16 bytes).  Wide slices
 // are split into chunks of `unit_width` slots whose partial sums are added in
 // chunk order by the last chunk to finish.  The row sums go out by MODE:
-//   kSellPlain  y[perm[pos]] = sum            (one SELL matrix)
-//   kSellFirst  ys[pos] = sum                  (column panels sharing one row
-//   kSellMid    ys[pos] += sum                  order: the partial sums stay in
-//   kSellLast   y[perm[pos]] = ys[pos] + sum    sorted order, coalesced, until
-//                                               the last panel scatters them)
+//   kSellPlain  y[perm[pos]] = sum    (one SELL matrix)
+//   kSellFirst  ys[pos] = sum          (column panels sharing one row order:
+//   kSellMid    ys[pos] += sum          the partial sums stay in sorted order,
+//                                       coalesced; a last pass puts them back
+//                                       in row order)
 struct SellArgs {
     const int2* units;
     const int64_t* slice_ptr;
@@ -386,7 +386,7 @@ struct SellArgs {
     double* ys;           // panels: partial sums per sorted position
 };
 
-enum SellOut : int { kSellPlain = 0, kSellFirst = 1, kSellMid = 2, kSellLast = 3 };
+enum SellOut : int { kSellPlain = 0, kSellFirst = 1, kSellMid = 2 };
 
 // perm and the sorted-order partial sums are streamed (evict-first loads,
 // streaming stores), so that they do not push x out of L2; the scattered y
@@ -396,8 +396,7 @@ template <int MODE>
 __device__ __forceinline__ void sell_put(const SellArgs& a, int64_t pos, double v) {
     if constexpr (MODE == kSellPlain) a.y[__ldcs(a.perm + pos)] = v;
     else if constexpr (MODE == kSellFirst) __stcs(a.ys + pos, v);
-    else if constexpr (MODE == kSellMid) __stcs(a.ys + pos, __ldcs(a.ys + pos) + v);
-    else a.y[__ldcs(a.perm + pos)] = __ldcs(a.ys + pos) + v;
+    else __stcs(a.ys + pos, __ldcs(a.ys + pos) + v);
 }
 
 template <int R, int MODE = kSellPlain>

@@ -34,6 +34,11 @@ __global__ void k_panel_group(const int32_t* __restrict__ ptr, int32_t m, int32_
     if (i < m) g[i] = gmax - (ptr[i + 1] - ptr[i] > long_len ? 0 : (int32_t)(1 + i / window));
 }
 
+__global__ void k_inverse_perm(const int32_t* __restrict__ perm, int32_t m, int32_t* __restrict__ ipos) {
+    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < m) ipos[perm[p]] = (int32_t)p;
+}
+
 // key[i] = maxlen - len[rows[i]]: the next key of a multi-key sort, in the
 // order the previous keys left.
 __global__ void k_gather_keys(const int32_t* __restrict__ len, const int32_t* __restrict__ rows, int32_t m,
@@ -355,6 +360,9 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
         SPMV_CUDA(cudaStreamSynchronize(s));
     }
     SPMV_TRY(h->alloc(&h->sell_ys, (size_t)m, nullptr));
+    SPMV_TRY(h->alloc(&h->sell_ipos, (size_t)m, nullptr));
+    k_inverse_perm<<<grid_for(m, 256), 256, 0, s>>>(h->perm, m, h->sell_ipos);
+    SPMV_CUDA(cudaGetLastError());
     int64_t slots = 0, ns = 0, nu = 0, maxlen = 0;
     for (int32_t p = 0; p < np; ++p) {
         const int32_t c0 = (int32_t)(p * pc), c1 = (int32_t)std::min<int64_t>(n, (int64_t)(p + 1) * pc);
@@ -451,17 +459,30 @@ static void sell_launch(const spmv_handle* h, const double* x, double* y, cudaSt
     }
 }
 
+// y[i] = ys[ipos[i]]: the panels' sums back in row order.  Rows in order
+// write whole sectors of y; the reads of ys stay inside a window of the
+// shared order at a time (or in the small region of the long rows), where
+// L2 serves the neighbouring entries.
+__global__ void __launch_bounds__(256) k_sell_unpermute(const int32_t* __restrict__ ipos, const double* __restrict__ ys,
+                                                        double* __restrict__ y, int32_t m) {
+    dev::pdl_wait();  // launched early (launch_pdl): wait for the last panel
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += stride)
+        __stcs(y + i, ys[__ldcs(ipos + i)]);
+}
+
 int sell_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s) {
     if (h->panels.empty()) {
         sell_launch<dev::kSellPlain>(h, x, y, s);
-    } else {  // ys = A_0 x_0, ys += A_p x_p, then y = ys + A_last x_last through the shared row order
+    } else {  // ys = A_0 x_0, ys += A_p x_p (p = 1 .. last), then y = ys through the shared row order
         const size_t np = h->panels.size();
         for (size_t p = 0; p < np; ++p) {
             const double* xp = x + (int64_t)p * h->panel_cols;
             if (p == 0) sell_launch<dev::kSellFirst>(h->panels[p], xp, y, s);
-            else if (p + 1 < np) sell_launch<dev::kSellMid>(h->panels[p], xp, y, s);
-            else sell_launch<dev::kSellLast>(h->panels[p], xp, y, s);
+            else sell_launch<dev::kSellMid>(h->panels[p], xp, y, s);
         }
+        launch_pdl(k_sell_unpermute, dim3((unsigned)grid_capped(h->m, 256, 8)), dim3(256), 0, s,
+                   (const int32_t*)h->sell_ipos, (const double*)h->sell_ys, y, h->m);
     }
     SPMV_CUDA(cudaGetLastError());
     return SPMV_OK;

@@ -28,7 +28,7 @@ def test_launches_per_run():
     assert bench.launches_per_run(1, _info(1, [3, 0, 0, 0])) == 1
     assert bench.launches_per_run(2, _info(2, [5, 0, 0, 0])) == 1
     assert bench.launches_per_run(3, _info(3, [5, 10, 3, 0], 32)) == 1
-    assert bench.launches_per_run(3, _info(3, [5, 10, 3, 3], 32)) == 3  # one per column panel
+    assert bench.launches_per_run(3, _info(3, [5, 10, 3, 3], 32)) == 4  # one per column panel, one unpermuting y
     assert bench.launches_per_run(4, _info(4, [2, 7, 3, 1])) == 2  # ELL part + tail
     assert bench.launches_per_run(4, _info(4, [2, 0, 3, 0])) == 1
 
