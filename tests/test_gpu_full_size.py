@@ -12,9 +12,9 @@ order, value bits).
     C = 32/64/128.
   * power-law graph n = 2e7 (239 M nonzeros): CSR, CSR5, HYB, SELL in its
     automatic column panels (x is 160 MB) and in one panel; ELL refused.
-  * the 512-matrix batch with the formats the batch model picks: every
-    matrix's y from the persistent launches equals its own product bit for
-    bit, and sampled rows of every matrix are within the FP64 bound.
+  * the 512-matrix batch with the formats the batch model picks, in both
+    persistent ways: every matrix's y equals its own product bit for bit,
+    and every row of every matrix is within the FP64 bound.
 """
 import os
 
@@ -23,7 +23,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import bits, row_subset, within_bound
+from gpu_util import bits
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -43,13 +43,6 @@ def sp():
 
 def _cores():
     return max(1, len(os.sched_getaffinity(0)))
-
-
-def _sample_rows(a, k=4096, extra=64):
-    lens = np.diff(a.ptr)
-    picks = [np.linspace(0, a.m - 1, k).astype(np.int64), np.argsort(lens, kind="stable")[-extra:],
-             np.argsort(lens, kind="stable")[:extra]]
-    return np.unique(np.concatenate(picks))
 
 
 def _all_rows(sp, a, x, cases, seed_note):
@@ -114,7 +107,11 @@ def test_graph_2e7_all_rows(sp):
     assert ei.value.name == "TOO_LARGE"
 
 
-def test_batch512_sampled_rows(sp):
+@pytest.mark.parametrize("one_launch", [False, True])
+def test_batch512_all_rows(sp, one_launch):
+    """The 512-matrix batch in the batch model's formats, both persistent ways:
+    every matrix's y equals its own product bit for bit, and every row of every
+    matrix is within the bound of the oracle's."""
     model = sp.Model.load(sp.MODEL_BATCH_PATH)
     handles, xs, ys, mats = [], [], [], []
     for j in range(512):
@@ -125,13 +122,15 @@ def test_batch512_sampled_rows(sp):
         ys.append(torch.empty(a.m, dtype=torch.float64, device="cuda"))
         mats.append(a)
         del d
-    b = sp.Batch(handles)
+    b = sp.Batch(handles, one_launch=one_launch)
     b.run(xs, ys)
     torch.cuda.synchronize()
     for j, (a, h) in enumerate(zip(mats, handles)):
         y = ys[j].cpu().numpy()
         single = sp.spmv_run(h, xs[j]).cpu().numpy()
         assert np.array_equal(bits(y), bits(single)), j
-        rows = _sample_rows(a, k=64, extra=8)
-        ok, msg = within_bound(row_subset(a, rows), xs[j].cpu().numpy(), y[rows])
-        assert ok, (j, msg)
+        x = xs[j].cpu().numpy()
+        ref = oracle.csr_spmv_threads(a, x, _cores())
+        bound = oracle.fp_bound(a, x)
+        bad = ~(np.abs(y - ref) <= bound)
+        assert not bad.any(), (j, int(np.argmax(bad)))
