@@ -314,10 +314,10 @@ int sell_convert(spmv_handle* h, const spmv_csr* c, cudaStream_t s) {
     // The order: rows longer than kPanelLongRow first, then the other rows in
     // windows of kPanelWindow consecutive rows; inside each group, rows sorted
     // by their panel lengths taken lexicographically (panel 0's first), which
-    // keeps every panel's slices nearly full.  The windows keep the last
-    // panel's writes of y within a window's few MiB, so that neighbouring
-    // rows meet in L2 and whole sectors go to memory (scattered over all of y,
-    // every 8-byte write costs a sector read and write).
+    // keeps every panel's slices nearly full.  The last pass writes y with
+    // the rows in order (whole sectors) and reads the sums through the order;
+    // the windows keep those reads within half a MiB of ys at a time, where L2
+    // serves the neighbouring entries.
     const int64_t np64 = ceil_div(n, pc);
     if (np64 > kPanelMax)
         return set_error(SPMV_ERR_INVALID_ARG, "%lld column panels requested; at most %d (sell_panel_cols >= %lld)",
