@@ -113,8 +113,8 @@ def algorithmic_bytes(fmt: int, info: dict) -> int:
         return base + aux[0] * (128 + 4 + 8 + 4 + 16)
     if fmt == 2:  # ELL: row_len
         return base + 4 * m
-    if fmt == 3:  # SELL: row_len, perm, slice_ptr, units
-        return base + 8 * m + 8 * (aux[0] + 1) + 8 * aux[1]
+    if fmt == 3:  # SELL: row_len, perm (not read when the sort moved no row: aux[3] = -1), slice_ptr, units
+        return base + (4 if aux[3] == -1 else 8) * m + 8 * (aux[0] + 1) + 8 * aux[1]
     # HYB: ELL row_len + tail row ids and pointers + read-modify-write of tail rows' y
     return base + 4 * m + 8 * aux[1] + 8 * aux[1]
 
@@ -301,8 +301,8 @@ def tuning_grid(fmt: int) -> list:
     if fmt == 1:
         return [{"csr5_sigma": 16}, {"csr5_sigma": 24}, {"csr5_sigma": 32}]
     if fmt == 3:
-        return [{"sell_C": 32, "sell_sigma": 1024}, {"sell_C": 32, "sell_sigma": -1}, {"sell_C": 64, "sell_sigma": -1},
-                {"sell_C": 128, "sell_sigma": -1}]
+        return [{"sell_C": 32, "sell_sigma": 1024}, {"sell_C": 32, "sell_sigma": -1}, {"sell_C": 64, "sell_sigma": 1},
+                {"sell_C": 64, "sell_sigma": -1}, {"sell_C": 128, "sell_sigma": -1}]
     if fmt == 0:  # the automatic path choice and the tiles
         return [{}, {"csr_block_nnz": 352}]
     return [{}]
@@ -476,11 +476,21 @@ def load_peaks() -> tuple:
     return (peak, "measured") if peak else (6800.0, "fallback")
 
 
-def load_traffic(key: str):
+def load_traffic(key: str, params: dict | None = None):
+    """DRAM bytes per launch from an ncu capture (profiles/traffic.json).  An
+    entry recorded with the tuning parameters of the captured launch counts
+    only for a handle with the same resolved parameters; otherwise null."""
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tr_path):
-        with open(tr_path) as fh:
-            return json.load(fh).get(key)
+    if not os.path.exists(tr_path):
+        return None
+    with open(tr_path) as fh:
+        v = json.load(fh).get(key)
+    if not isinstance(v, (dict, list)):
+        return v
+    for e in v if isinstance(v, list) else [v]:
+        want = e.get("params", {})
+        if params is not None and all(params.get(k) == w for k, w in want.items()):
+            return e["bytes"]
     return None
 
 
@@ -497,6 +507,7 @@ class Workload:
         import synth
 
         self.name, self.sp, self.torch, self.stream, self.flush = name, sp, torch, stream, flush
+        self.fixed_params = args.params if name == args.workload else None
         full = make_matrix(name)
         self.total_nnz, self.total_rows = full.nnz, full.m
         if world > 1:
@@ -607,10 +618,13 @@ class Workload:
         # ---- the selected format's parameters from the autotuner's grid
         # (one-off setup, like the conversion): the fastest of the default and the grid
         hc = handles[chosen]
+        fixed = json.loads(self.fixed_params) if self.fixed_params else None
+        if fixed is not None:  # --params: these parameters, no search (profiling the kernel a run picked)
+            hc = sp.spmv_convert(chosen, d, fixed)
         tune_runs = max(10, min(self.format_steps, 50))
         tune_ms = statistics.mean(self.timed(lambda: sp.spmv_run(hc, x, y), tune_runs, 3))
-        tuning = [{"params": "default", "ms": tune_ms}]
-        for p in tuning_grid(chosen):
+        tuning = [{"params": fixed if fixed is not None else "default", "ms": tune_ms}]
+        for p in tuning_grid(chosen) if fixed is None else []:
             if not p:
                 continue
             try:
@@ -677,7 +691,7 @@ class Workload:
         ab = algorithmic_bytes(self.chosen, self.info_c)
         achieved = ab / kms / 1e6
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": load_traffic(f"{self.name}:{FORMATS[self.chosen]}"),
+                "traffic": load_traffic(f"{self.name}:{FORMATS[self.chosen]}", self.info_c["params"]),
                 "kernel": f"{FORMATS[self.chosen]} product", "kernel_ms": kms,
                 "kernel_ms_source": "CUDA events around the product in a second pass of the same steps",
                 "alg_bytes_per_launch": ab, "peak_source": f"{src} hbm_gbs (STREAM-style copy, burst)",
@@ -743,6 +757,9 @@ def main():
     ap.add_argument("--batch-extra", type=int, default=32,
                     help="after the headline: the first N matrices of the batched configuration as an extra key (0: none)")
     ap.add_argument("--batch-format", type=int, default=-1, help="batch512: one format for every matrix (-1: selector)")
+    ap.add_argument("--params", default=None,
+                    help="JSON tuning parameters of the headline workload's selected format, used as given "
+                         "instead of the autotuner's search (for profiling one kernel)")
     ap.add_argument("--no-graph", action="store_true", help="launch the timed steps directly instead of replaying a CUDA graph")
     args = ap.parse_args()
 

@@ -122,7 +122,9 @@ typedef struct {
                                CSR  {warp tiles, lanes per row (0: the tiles run), 0, 0}
                                CSR5 {tiles, tiles listing their rows, empty rows, 0}
                                ELL  {K, rows left to whole blocks, their length threshold, 0}
-                               SELL {slices, warp units, longest row, column panels (0: one)}
+                               SELL {slices, warp units, longest row, column panels: 0 one
+                                     panel; -1 one panel whose sort moved no row, so that
+                                     the product writes y without reading perm}
                                HYB  {COO tail entries, tail rows, K, tail warp tiles} */
 } spmv_info;
 

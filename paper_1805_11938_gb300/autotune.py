@@ -108,7 +108,7 @@ def default_grid(fmt: int, m: int) -> list:
     if fmt == SPMV_SELL:
         out = []
         for C in (32, 64, 128):
-            for sig in (C, 32 * C, 1024 * C, -1):
+            for sig in (1, 32 * C, 1024 * C, -1):  # sigma = 1 keeps the rows in place (no perm read)
                 if sig == -1 or sig < m:
                     out.append({"sell_C": C, "sell_sigma": sig})
         return out

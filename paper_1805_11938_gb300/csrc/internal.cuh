@@ -143,6 +143,7 @@ struct spmv_handle {
     // its entry j (for the way back).  ptr keeps the CSR row pointers.
     double* sell_ys = nullptr;
     int32_t* sell_ipos = nullptr;  // panels: row -> sorted position (the inverse of perm)
+    bool sell_ident = false;       // one panel whose sort moved no row: y written without perm
     int32_t panel_cols = 0;
     std::vector<spmv_handle*> panels;
     std::vector<int32_t*> panel_pos;

@@ -386,7 +386,7 @@ struct SellArgs {
     double* ys;           // panels: partial sums per sorted position
 };
 
-enum SellOut : int { kSellPlain = 0, kSellFirst = 1, kSellMid = 2 };
+enum SellOut : int { kSellPlain = 0, kSellFirst = 1, kSellMid = 2, kSellIdent = 3 };
 
 // perm and the sorted-order partial sums are streamed (evict-first loads,
 // streaming stores), so that they do not push x out of L2; the scattered y
@@ -395,6 +395,7 @@ enum SellOut : int { kSellPlain = 0, kSellFirst = 1, kSellMid = 2 };
 template <int MODE>
 __device__ __forceinline__ void sell_put(const SellArgs& a, int64_t pos, double v) {
     if constexpr (MODE == kSellPlain) a.y[__ldcs(a.perm + pos)] = v;
+    else if constexpr (MODE == kSellIdent) __stcs(a.y + pos, v);  // the sort left every row in place
     else if constexpr (MODE == kSellFirst) __stcs(a.ys + pos, v);
     else __stcs(a.ys + pos, __ldcs(a.ys + pos) + v);
 }

@@ -69,13 +69,16 @@ __global__ void k_bit_scatter(const uint32_t* __restrict__ key, const int32_t* _
     row2[pos] = row[i];
 }
 
+// moved: set to 1 (by every writer alike) when some row left its place
 __global__ void k_sorted_len(const int32_t* __restrict__ len, const int32_t* __restrict__ perm, int32_t m,
-                             int64_t mp, int32_t* __restrict__ sl, int32_t* __restrict__ ipos) {
+                             int64_t mp, int32_t* __restrict__ sl, int32_t* __restrict__ ipos,
+                             int32_t* __restrict__ moved) {
     int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p < m) {
         const int32_t r = perm[p];
         sl[p] = len[r];
         ipos[r] = (int32_t)p;
+        if (r != p) *moved = 1;
     } else if (p < mp) {
         sl[p] = 0;
     }
@@ -191,7 +194,10 @@ static int sell_build(spmv_handle* h, const spmv_csr* c, cudaStream_t s, int32_t
     const int64_t mp = ns * C;
     h->n_slices = ns;
     SPMV_TRY(h->alloc(&h->sell_len, (size_t)mp, "row_len"));
-    k_sorted_len<<<grid_for(mp, 256), 256, 0, s>>>(len, h->perm, m, mp, h->sell_len, ipos);
+    int32_t* moved = nullptr;
+    SPMV_TRY(tmp.get(&moved, 1));
+    SPMV_CUDA(cudaMemsetAsync(moved, 0, sizeof(int32_t), s));
+    k_sorted_len<<<grid_for(mp, 256), 256, 0, s>>>(len, h->perm, m, mp, h->sell_len, ipos, moved);
     int64_t* cw = nullptr;
     int32_t *nunit = nullptr, *uoff = nullptr;
     SPMV_TRY(tmp.get(&cw, (size_t)ns + 1));
@@ -203,10 +209,14 @@ static int sell_build(spmv_handle* h, const spmv_csr* c, cudaStream_t s, int32_t
     SPMV_TRY(exclusive_scan<int64_t>(cw, h->slice_ptr, ns, s, tmp));
     SPMV_TRY(exclusive_scan<int32_t>(nunit, uoff, ns + 1, s, tmp));
     int64_t total = 0;
-    int32_t nu = 0;
+    int32_t nu = 0, moved_h = 1;
     SPMV_CUDA(cudaMemcpyAsync(&total, h->slice_ptr + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     SPMV_CUDA(cudaMemcpyAsync(&nu, uoff + ns, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SPMV_CUDA(cudaMemcpyAsync(&moved_h, moved, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     SPMV_CUDA(cudaStreamSynchronize(s));
+    // a sort that moved no row (sigma = 1, or rows already in order): the
+    // product writes y at the sorted positions and never reads perm
+    h->sell_ident = perm_in == nullptr && moved_h == 0;
     const int64_t bytes = total * 12 + mp * 8 + (int64_t)nu * (C * 8 + 12);
     const int64_t cap = resolve_cap(h->params);
     if (bytes > cap)
@@ -234,6 +244,7 @@ static int sell_build(spmv_handle* h, const spmv_csr* c, cudaStream_t s, int32_t
     h->aux[0] = ns;
     h->aux[1] = nu;
     h->aux[2] = maxlen;
+    h->aux[3] = h->sell_ident ? -1 : 0;
     return SPMV_OK;
 }
 
@@ -473,7 +484,8 @@ __global__ void __launch_bounds__(256) k_sell_unpermute(const int32_t* __restric
 
 int sell_run(const spmv_handle* h, const double* x, double* y, cudaStream_t s) {
     if (h->panels.empty()) {
-        sell_launch<dev::kSellPlain>(h, x, y, s);
+        if (h->sell_ident) sell_launch<dev::kSellIdent>(h, x, y, s);
+        else sell_launch<dev::kSellPlain>(h, x, y, s);
     } else {  // ys = A_0 x_0, ys += A_p x_p (p = 1 .. last), then y = ys through the shared row order
         const size_t np = h->panels.size();
         for (size_t p = 0; p < np; ++p) {

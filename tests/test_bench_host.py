@@ -28,6 +28,7 @@ def test_launches_per_run():
     assert bench.launches_per_run(1, _info(1, [3, 0, 0, 0])) == 1
     assert bench.launches_per_run(2, _info(2, [5, 0, 0, 0])) == 1
     assert bench.launches_per_run(3, _info(3, [5, 10, 3, 0], 32)) == 1
+    assert bench.launches_per_run(3, _info(3, [5, 10, 3, -1], 32)) == 1  # rows in place: one kernel too
     assert bench.launches_per_run(3, _info(3, [5, 10, 3, 3], 32)) == 4  # one per column panel, one unpermuting y
     assert bench.launches_per_run(4, _info(4, [2, 7, 3, 1])) == 2  # ELL part + tail
     assert bench.launches_per_run(4, _info(4, [2, 0, 3, 0])) == 1
@@ -46,6 +47,8 @@ def test_algorithmic_bytes_closed_forms():
     assert bench.algorithmic_bytes(1, info([5, 0, 0, 0])) == base + 5 * 160          # CSR5: 160 B per tile
     assert bench.algorithmic_bytes(2, info([7, 0, 0, 0])) == base + 4 * m            # ELL: row_len
     assert bench.algorithmic_bytes(3, info([32, 40, 9, 0])) == base + 8 * m + 8 * 33 + 8 * 40  # SELL
+    # SELL whose sort moved no row (aux[3] = -1): row_len only, perm is not read
+    assert bench.algorithmic_bytes(3, info([32, 40, 9, -1])) == base + 4 * m + 8 * 33 + 8 * 40
     assert bench.algorithmic_bytes(4, info([2, 30, 3, 1])) == base + 4 * m + 16 * 30  # HYB: 16 B per tail row
     # the padding a layout stores does not count: the same matrix in ELL moves the same nonzeros
     assert bench.algorithmic_bytes(2, info([7000, 0, 0, 0])) == bench.algorithmic_bytes(2, info([7, 0, 0, 0]))
@@ -66,3 +69,24 @@ def test_clock_sampler_summary():
     assert cs2.summary()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
     assert bench.ClockSampler(0).summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"],
                                                "samples": 0}
+
+
+def test_traffic_counts_only_for_the_captured_parameters(tmp_path, monkeypatch):
+    """An ncu traffic figure recorded with the captured launch's tuning
+    parameters is reported only for a handle resolved to the same ones."""
+    import json
+
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({
+        "w:SELL": [{"bytes": 10, "params": {"sell_C": 64, "sell_sigma": 1}},
+                   {"bytes": 20, "params": {"sell_C": 64, "sell_sigma": 500}}],
+        "w:CSR5": {"bytes": 30, "params": {"csr5_sigma": 32}},
+        "w:CSR": 40}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_traffic("w:SELL", {"sell_C": 64, "sell_sigma": 1, "hyb_k": 0}) == 10
+    assert bench.load_traffic("w:SELL", {"sell_C": 64, "sell_sigma": 500}) == 20
+    assert bench.load_traffic("w:SELL", {"sell_C": 32, "sell_sigma": 1}) is None
+    assert bench.load_traffic("w:CSR5", {"csr5_sigma": 24}) is None
+    assert bench.load_traffic("w:CSR5", {"csr5_sigma": 32}) == 30
+    assert bench.load_traffic("w:CSR", {}) == 40
+    assert bench.load_traffic("w:ELL", {}) is None

@@ -177,7 +177,8 @@ def test_sell_panel_rule_splits_large_x():
     ok, msg = within_bound(a, x, y)
     assert ok, msg
     h1, y1 = _run(a, 3, {"sell_panel_cols": -1}, x)
-    assert h1.info()["aux"][3] == 0 and h1.info()["params"]["sell_panel_cols"] == a.n
+    # one panel; every row 5 long, so the sort moved no row (aux[3] = -1)
+    assert h1.info()["aux"][3] == -1 and h1.info()["params"]["sell_panel_cols"] == a.n
     assert within_bound(a, x, y1)[0]
 
 
@@ -235,6 +236,26 @@ def test_sell_layout_matches_oracle(C, sigma, mi):
     assert np.array_equal(_np(h.array("slice_ptr")), s["slice_ptr"])
     assert np.array_equal(_np(h.array("col")), s["col"])
     assert np.array_equal(bits(_np(h.array("val")).view(np.float64)), bits(s["val"]))
+    # the product skips perm exactly when the oracle's order is the identity
+    assert h.info()["aux"][3] == (-1 if np.array_equal(s["perm"], np.arange(a.m)) else 0)
+
+
+@pytest.mark.parametrize("C,sigma", [(32, 1), (64, 1), (128, 1), (64, -1), (32, 64)])
+def test_sell_identity_order_runs_without_perm(C, sigma):
+    """Rows the sort leaves in place (sigma = 1, or equal lengths under any
+    sigma): the handle reports it (aux[3] = -1) and the product, writing y
+    without perm, matches the oracle; a matrix the sort reorders keeps perm."""
+    m = 1000
+    same = synth.uniform_random(m, 7, 3)  # every row 7 long: no sort moves a row
+    mixed = synth.powerlaw(m, 11)
+    for a, ident in ((same, True), (mixed, sigma == 1)):
+        x = synth.vector(a.n, 5)
+        h, y = _run(a, 3, {"sell_C": C, "sell_sigma": sigma}, x)
+        s = oracle.to_sell(a, C, a.m if sigma == -1 else sigma)
+        assert np.array_equal(s["perm"], np.arange(a.m)) == ident
+        assert h.info()["aux"][3] == (-1 if ident else 0)
+        ref = oracle.csr_spmv(a, x)
+        assert np.all(np.abs(y - ref) <= oracle.fp_bound(a, x))
 
 
 @pytest.mark.parametrize("mi", [1, 2, 3, 9])

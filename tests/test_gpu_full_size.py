@@ -9,7 +9,7 @@ order, value bits).
     autotuner's grid (CSR tiles, CSR5 sigma 16/24/32, SELL C = 32/64/128),
     ELL at the benchmark's 160 GiB cap (its padded layout is about 119 GB).
   * 27-point stencil on 224^3 (300.8 M nonzeros): all five formats, SELL at
-    C = 32/64/128.
+    C = 32/64/128 and at C = 64 with sigma = 1 (rows in place, no perm read).
   * power-law graph n = 2e7 (239 M nonzeros): CSR, CSR5, HYB, SELL in its
     automatic column panels (x is 160 MB) and in one panel; ELL refused.
   * the 512-matrix batch with the formats the batch model picks, in both
@@ -89,7 +89,8 @@ def test_power_law_2e6_all_rows_every_format(sp):
 def test_stencil_224_all_rows_every_format(sp):
     a = synth.config5_stencil()
     x = synth.vector(a.n, 1)
-    cases = [(0, None), (1, None), (2, None), (3, None), (3, {"sell_C": 64}), (3, {"sell_C": 128}), (4, None)]
+    cases = [(0, None), (1, None), (2, None), (3, None), (3, {"sell_C": 64}), (3, {"sell_C": 64, "sell_sigma": 1}),
+             (3, {"sell_C": 128}), (4, None)]
     fails, _ = _all_rows(sp, a, x, cases, "stencil 224^3")
     assert not fails, fails
 
