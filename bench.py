@@ -834,44 +834,27 @@ def main():
     w.flush = flush
     del dirty
 
-    # ---- end to end: every step copies its x in from pinned host memory, runs
-    # the step through the library, and copies its y out.  x and y are
-    # double-buffered and the copies run on two copy streams (in and out), so
-    # one step's copies overlap the neighbouring steps' compute; every step
-    # still moves its own 16 bytes per row.  The working set (the matrix)
-    # exceeds L2, so no flush between steps.
+    # ---- end to end through the library's host-memory call (spmv_run_host):
+    # every step copies its x in from pinned host memory, runs the step, and
+    # copies its y out.  The io alternates between two device staging pairs
+    # and copies on two streams of its own (in and out), so one step's copies
+    # overlap the neighbouring steps' compute; every step still moves its own
+    # 16 bytes per row.  The working set (the matrix) exceeds L2, so no flush
+    # between steps.
     n_e2e = max(10, min(args.steps, 500))
     xh_pin = [torch.as_tensor(xh).pin_memory() for _ in range(2)]
     yh_pin = [torch.empty(a.m, dtype=torch.float64).pin_memory() for _ in range(2)]
-    xb = [torch.empty_like(x) for _ in range(2)]
-    yb = [torch.empty_like(y) for _ in range(2)]
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    io = sp.HostIO(w.hc)
 
     def e2e_run(n):
-        ev = [[torch.cuda.Event() for _ in range(3)] for _ in range(n)]  # copied in, computed, copied out
         t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t1.record(stream)  # created now; recorded again after the last copy out
         torch.cuda.synchronize()
         t0.record(stream)
-        s_in.wait_event(t0)
         for i in range(n):
             b = i % 2
-            with torch.cuda.stream(s_in):
-                if i >= 2:
-                    s_in.wait_event(ev[i - 2][1])  # buffer b's previous product has read its x
-                xb[b].copy_(xh_pin[b], non_blocking=True)
-                ev[i][0].record(s_in)
-            stream.wait_event(ev[i][0])
-            if i >= 2:
-                stream.wait_event(ev[i - 2][2])  # buffer b's previous y has been copied out
             w.select_step()
-            sp.spmv_run(w.hc, xb[b], yb[b])
-            ev[i][1].record(stream)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev[i][1])
-                yh_pin[b].copy_(yb[b], non_blocking=True)
-                ev[i][2].record(s_out)
-        stream.wait_event(ev[n - 1][2])
-        t1.record(stream)
+            io.run(xh_pin[b], yh_pin[b], stream, done=t1 if i == n - 1 else None)
         t1.synchronize()
         return t0.elapsed_time(t1) / n
 
@@ -885,7 +868,7 @@ def main():
     if model is not None:
         torch.cuda.synchronize()
         agree = FORMATS[int(w.fmt_dev.item())] == w.selector["pick"]
-    del xb, yb, xh_pin, yh_pin
+    del io, xh_pin, yh_pin
 
     kms = statistics.mean(kern_ms)
     summ = w.summary(total_ms / args.steps, kms)
@@ -908,8 +891,9 @@ def main():
         "roofline": summ["roofline"],
         "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * a.n * world,
                 "d2h_bytes_per_step": 8 * w.total_rows, "ms_per_step": e2e_ms, "steps": n_e2e,
-                "copies": "pinned host x in and y out every step, double-buffered on two copy streams "
-                          "(overlapping the neighbouring steps' compute)", "y_matches_device_run": e2e_same},
+                "copies": "spmv_run_host: pinned host x in and y out every step, through two device staging "
+                          "pairs and two copy streams of the library (overlapping the neighbouring steps' "
+                          "compute)", "y_matches_device_run": e2e_same},
         "gpu_launches": world * args.steps * (SELECT_LAUNCHES + launches_per_run(w.chosen, w.info_c)),
         "clocks": clocks,
         "formats": w.per_fmt,

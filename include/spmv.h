@@ -257,6 +257,38 @@ SPMV_API int spmv_mlp_train(float* theta_dev, float* m_dev, float* v_dev, const 
 SPMV_API int spmv_mlp_forward(const float* theta_dev, const float* X_dev, int32_t B, float* logits_dev,
                      int32_t* pred_dev, cudaStream_t stream);
 
+/* ------------------------------------------------- x and y in host memory */
+
+/* Products whose x and y live in host memory (Sec. II-A's y = A x with the
+ * copies in and out included).  An spmv_host_io holds, for one handle, two
+ * device staging pairs (x: N doubles, y: M doubles) and two copy streams of
+ * its own (in and out).  create allocates them on the handle's device (so it
+ * is not for stream capture); the handle must outlive the io.  Errors:
+ * INVALID_ARG, ALLOC, CUDA. */
+typedef struct spmv_host_io spmv_host_io;
+SPMV_API int spmv_host_io_create(const spmv_handle* h, spmv_host_io** out);
+
+/* y_host = A x_host.  Copies x_host (N doubles) into a staging buffer on the
+ * copy-in stream, runs spmv_run on `stream` once that copy is done, and
+ * copies y to y_host (M doubles) on the copy-out stream once the product is
+ * done.  Calls alternate between the two staging pairs, so one call's copies
+ * overlap the products of the calls before and after it; a call waits on the
+ * device (never on the host) for the call two before it to release its pair.
+ * Returns at once.  `done` (may be NULL): an event recorded after the copy
+ * out; once it has completed, y_host holds y and x_host may be rewritten.
+ * With pinned host memory the copies are asynchronous; pageable memory works,
+ * with copies that CUDA may stage.  Calls on one io must come from one host
+ * thread at a time; products of one handle run in call order.  Errors:
+ * INVALID_ARG (NULL io or buffers), CUDA. */
+SPMV_API int spmv_run_host(spmv_host_io* io, const double* x_host, double* y_host, cudaStream_t stream,
+                           cudaEvent_t done);
+
+/* Blocks the host until every copy out issued through `io` has completed. */
+SPMV_API int spmv_host_io_sync(spmv_host_io* io);
+
+/* Waits for the io's copies, then releases its buffers and streams. */
+SPMV_API void spmv_host_io_free(spmv_host_io* io);
+
 /* ------------------------------------------------------------- batching */
 
 /* Many independent products y_b = A_b x_b in one CUDA graph of persistent

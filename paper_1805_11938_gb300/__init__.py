@@ -26,7 +26,8 @@ __all__ = [
     "SpmvError", "DeviceCSR", "Handle", "Model", "Batch", "spmv_convert", "spmv_run", "spmv_to_csr",
     "spmv_features", "spmv_select", "spmv_select_async", "spmv_mlp_scale", "spmv_mlp_loss_grad", "spmv_mlp_adam",
     "spmv_mlp_train", "spmv_mlp_forward", "spmv_batch_build", "spmv_batch_run", "spmv_batch_run_separate",
-    "spmv_csr_run_noalloc", "spmv_debug_fail_alloc", "spmv_debug_features_cluster", "lib",
+    "spmv_csr_run_noalloc", "spmv_debug_fail_alloc", "spmv_debug_features_cluster", "lib", "HostIO",
+    "spmv_host_io_create", "spmv_run_host",
 ]
 
 
@@ -272,6 +273,47 @@ def spmv_mlp_forward(theta, X, stream=None):
     pred = torch.empty(B, dtype=torch.int32, device="cuda")
     check(lib().spmv_mlp_forward(_vp(theta), _vp(X), B, _vp(logits), _vp(pred), _stream(stream)), "spmv_mlp_forward")
     return logits, pred
+
+
+class HostIO:
+    """Products of one handle with x and y in host memory (include/spmv.h,
+    spmv_run_host): two device staging pairs used in turn and two copy
+    streams, so one call's copies overlap the neighbouring calls' products."""
+
+    def __init__(self, h: Handle):
+        self.h = h  # the handle must outlive the io
+        out = ctypes.c_void_p()
+        check(lib().spmv_host_io_create(h.raw, ctypes.byref(out)), "spmv_host_io_create")
+        self._io = out
+
+    def run(self, x_host, y_host, stream=None, done=None):
+        """y_host = A x_host (float64 CPU tensors, pinned for asynchronous copies).
+        Returns at once; y_host holds the result after sync(), or once the
+        torch.cuda.Event `done` has completed."""
+        torch = _torch()
+        for t, n, what in ((x_host, self.h.n, "x_host"), (y_host, self.h.m, "y_host")):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != n:
+                raise ValueError(f"{what} must be a contiguous float64 CPU tensor of {n} elements")
+        if done is not None and not done.cuda_event:
+            done.record()  # torch creates its events at their first record
+        ev = ctypes.c_void_p(done.cuda_event) if done is not None else None
+        check(lib().spmv_run_host(self._io, _vp(x_host), _vp(y_host), _stream(stream), ev), "spmv_run_host")
+
+    def sync(self):
+        check(lib().spmv_host_io_sync(self._io), "spmv_host_io_sync")
+
+    def __del__(self):
+        if getattr(self, "_io", None) and self._io.value and _abi._lib is not None:
+            _abi._lib.spmv_host_io_free(self._io)
+            self._io = None
+
+
+def spmv_host_io_create(h: Handle) -> HostIO:
+    return HostIO(h)
+
+
+def spmv_run_host(io: HostIO, x_host, y_host, stream=None, done=None):
+    io.run(x_host, y_host, stream, done)
 
 
 class Batch:

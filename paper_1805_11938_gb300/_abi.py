@@ -77,6 +77,10 @@ _SIGS = {
     "spmv_mlp_adam": (ctypes.c_int, [_VP, _VP, _VP, _VP, _I32, _I32, _F, _F, _F, _F, _VP]),
     "spmv_mlp_train": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _I32, _I32, _I32, _F, _F, _F, _F, _VP, _VP]),
     "spmv_mlp_forward": (ctypes.c_int, [_VP, _VP, _I32, _VP, _VP, _VP]),
+    "spmv_host_io_create": (ctypes.c_int, [_VP, ctypes.POINTER(_VP)]),
+    "spmv_run_host": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "spmv_host_io_sync": (ctypes.c_int, [_VP]),
+    "spmv_host_io_free": (None, [_VP]),
     "spmv_batch_build": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _VP, ctypes.POINTER(_VP)]),
     "spmv_batch_build_ex": (ctypes.c_int, [ctypes.POINTER(_VP), _I32, _I32, _VP, ctypes.POINTER(_VP)]),
     "spmv_batch_launches": (ctypes.c_int, [_VP, ctypes.POINTER(_I32)]),
