@@ -1,7 +1,9 @@
 // SELL-C-sigma (Sec. II-B "SELL and SELL-C-sigma"): rows are sorted by
 // length, descending and stably, inside windows of sigma rows; consecutive
 // groups of C sorted rows form slices, each stored as a column-major ELL of
-// its own width.  sigma = 1 is plain SELL.
+// its own width.  sigma = 1 is plain SELL.  The product writes y[perm[p]]
+// for the row at sorted position p, or y[p] directly when the sort moved no
+// row (sigma = 1, or rows already in order), so that perm is not read.
 //
 // Conversion on the device: a stable segmented LSD radix sort (one bit per
 // pass, a scan and a scatter each) orders every window by (maxlen - length);
