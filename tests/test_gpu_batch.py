@@ -30,7 +30,8 @@ def _mats(n):
 
 @pytest.mark.parametrize("one_launch", [False, True])
 @pytest.mark.parametrize("params", [None, {"csr5_sigma": 4, "sell_C": 128, "sell_sigma": 256, "hyb_k": 2},
-                                    {"csr_block_nnz": -8}, {"csr_block_nnz": 352}])
+                                    {"csr_block_nnz": -8}, {"csr_block_nnz": 352},
+                                    {"sell_C": 64, "sell_sigma": 1}])  # SELL rows in place: run writes y without perm
 def test_batch_matches_single_runs(sp, params, one_launch):
     mats = _mats(23)
     handles, xs, ys, ys2, singles = [], [], [], [], []
