@@ -497,7 +497,7 @@ def load_traffic(key: str, params: dict | None = None):
 class Workload:
     """One matrix resident in HBM, measured the way the headline step runs:
     every format converted and timed on its own (the exhaustive search, also
-    the selector's judge), the selector's pick and its autotuned parameters,
+    the yardstick of the selector), the selector's pick and its autotuned parameters,
     the step (selector kernel + product, one CUDA graph) timed with the L2
     flushed before every step, the product kernel's own duration, the gather
     ceiling of the matrix's index stream, and every row of the result checked
