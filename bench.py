@@ -859,8 +859,11 @@ def main():
         return t0.elapsed_time(t1) / n
 
     e2e_run(5)
-    barrier()
-    e2e_ms = e2e_run(n_e2e)
+    e2e_windows = []
+    for _ in range(3):  # the copies cross host memory that other processes share: median of three windows
+        barrier()
+        e2e_windows.append(e2e_run(n_e2e))
+    e2e_ms = statistics.median(e2e_windows)
     torch.cuda.synchronize()
     e2e_ms, e2e_value = reduce_over_ranks(e2e_ms, 2.0 * a.nnz, dist, dist_backend()[1])
     e2e_same = bool(np.array_equal(yh_pin[(n_e2e - 1) % 2].numpy(), y.cpu().numpy()))
@@ -891,6 +894,7 @@ def main():
         "roofline": summ["roofline"],
         "e2e": {"value": e2e_value, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * a.n * world,
                 "d2h_bytes_per_step": 8 * w.total_rows, "ms_per_step": e2e_ms, "steps": n_e2e,
+                "windows_ms_per_step": e2e_windows, "of": "the median of three windows of `steps` steps",
                 "copies": "spmv_run_host: pinned host x in and y out every step, through two device staging "
                           "pairs and two copy streams of the library (overlapping the neighbouring steps' "
                           "compute)", "y_matches_device_run": e2e_same},
