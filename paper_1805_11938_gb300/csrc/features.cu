@@ -15,8 +15,8 @@
 //
 // Two launches.  k_rowstats reads ptr once with the whole GPU and reduces the
 // exact statistics (min, max, sum of squares, empty rows, rows of length >= 32)
-// into one slot of a small static device array, its last block to finish
-// publishing them.  The features kernel, launched behind it with
+// into one slot of a small static device array (each block adds its totals
+// with relaxed atomics and exits).  The features kernel, launched behind it with
 // programmatic stream serialization, is one thread-block cluster (16 CTAs x
 // 512 threads where the device can place one, else 8 x 1024), one sampled row
 // per thread.  Each CTA reduces its rows, then adds its statistics and its
@@ -164,17 +164,15 @@ __device__ int mlp_forward_64(const float* th, const float* xs, float* h1, float
 
 // ------------------------------------------------------- exact row lengths
 //
-// One slot of the ring holds one call's accumulators (reset to zero by the
-// call's last block, so every call finds them at zero) and its published
-// totals.  Calls take slots in turn on the host, so up to kRowSlots calls may
-// be in flight on one device at once; a CUDA graph replays the slot it
-// captured.  The minimum is accumulated as the maximum of ~len, so that zero
-// is the identity of every accumulator.
-struct __align__(64) RowStatsSlot {
+// One slot of the ring holds one call's accumulators.  The features kernel
+// reads them once k_rowstats has completed and sets them back to zero, so
+// every call finds its slot at zero.  Calls take slots in turn on the host, so
+// up to kRowSlots calls may be in flight on one device at once; a CUDA graph
+// replays the slot it captured.  The minimum is accumulated as the maximum of
+// ~len, so that zero is the identity of every accumulator.
+struct __align__(32) RowStatsSlot {
     unsigned long long acc_sq;
-    unsigned acc_max, acc_cmin, acc_empty, acc_long, ticket, pad0;
-    unsigned long long fin_sq;
-    unsigned fin_max, fin_min, fin_empty, fin_long;
+    unsigned acc_max, acc_cmin, acc_empty, acc_long;
 };
 constexpr int kRowSlots = 64;
 static __device__ RowStatsSlot g_rowstats[kRowSlots];
@@ -263,15 +261,6 @@ __global__ void __launch_bounds__(kRowStatsThreads, 6) k_rowstats(const int32_t*
         ref_u(slot->acc_empty).fetch_add(emp, cuda::memory_order_relaxed);
         ref_u(slot->acc_long).fetch_add(lng, cuda::memory_order_relaxed);
         ref_ull(slot->acc_sq).fetch_add(sq, cuda::memory_order_relaxed);
-        // release this block's additions; the last block acquires everyone's
-        const unsigned prev = ref_u(slot->ticket).fetch_add(1u, cuda::memory_order_acq_rel);
-        if (prev != gridDim.x - 1) return;
-        slot->fin_max = ref_u(slot->acc_max).exchange(0u, cuda::memory_order_relaxed);
-        slot->fin_min = ~ref_u(slot->acc_cmin).exchange(0u, cuda::memory_order_relaxed);
-        slot->fin_empty = ref_u(slot->acc_empty).exchange(0u, cuda::memory_order_relaxed);
-        slot->fin_long = ref_u(slot->acc_long).exchange(0u, cuda::memory_order_relaxed);
-        slot->fin_sq = ref_ull(slot->acc_sq).exchange(0ull, cuda::memory_order_relaxed);
-        ref_u(slot->ticket).store(0u, cuda::memory_order_relaxed);
     }
 }
 
@@ -282,7 +271,7 @@ __global__ void __launch_bounds__(kRowStatsThreads, 6) k_rowstats(const int32_t*
 template <int CTAS, bool VEC>
 __global__ void __launch_bounds__(kSample / CTAS)
     k_features(const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx, int32_t m, int32_t n, int64_t nnz,
-               const RowStatsSlot* __restrict__ rs, float* __restrict__ feat_out,
+               RowStatsSlot* __restrict__ rs, float* __restrict__ feat_out,
                const float* __restrict__ model_params, const float* __restrict__ lo, const float* __restrict__ hi,
                int64_t ell_cap, int32_t* __restrict__ fmt_out, float* __restrict__ logits_out) {
     constexpr int T = kSample / CTAS;
@@ -488,9 +477,14 @@ __global__ void __launch_bounds__(kSample / CTAS)
         const int j = lane & 15;
         const unsigned long long spread_sum = tot_u[1];
         const unsigned long long sum_len = (unsigned long long)(unsigned)nnz_sm;  // exact, all rows
-        const unsigned long long sum_sq = rs->fin_sq;
-        const int min_len = (int)rs->fin_min, max_len = (int)rs->fin_max, bandw = tot_band;
-        const unsigned empty = rs->fin_empty, longc = rs->fin_long, spread_cnt = tot_cnt;
+        const unsigned long long sum_sq = rs->acc_sq;
+        const int min_len = (int)~rs->acc_cmin, max_len = (int)rs->acc_max, bandw = tot_band;
+        const unsigned empty = rs->acc_empty, longc = rs->acc_long, spread_cnt = tot_cnt;
+        __syncwarp();
+        if (lane == 0) {  // the slot starts the next call that takes it at zero
+            rs->acc_sq = 0ull;
+            rs->acc_max = rs->acc_cmin = rs->acc_empty = rs->acc_long = 0u;
+        }
         const unsigned rows = (unsigned)m;
         const float fc = (float)m;
         const float nz = (float)nnz_sm;
@@ -551,7 +545,7 @@ __global__ void __launch_bounds__(kSample / CTAS)
 // The features kernel, launched behind k_rowstats with programmatic stream
 // serialization (its sampled part overlaps the exact pass over ptr).
 template <int CTAS, bool VEC>
-static cudaError_t launch_features_k(const spmv_csr* c, const RowStatsSlot* rs, float* feat, const spmv_model* model,
+static cudaError_t launch_features_k(const spmv_csr* c, RowStatsSlot* rs, float* feat, const spmv_model* model,
                                      int32_t* fmt, float* logits, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(CTAS, 1, 1);
@@ -658,7 +652,12 @@ static int launch_features(const spmv_csr* c, float* feat, const spmv_model* mod
                                        : launch_features_k<kFeatCtasLarge, false>(c, rs, feat, model, fmt, logits, s))
                                 : (vec ? launch_features_k<kFeatCtasSmall, true>(c, rs, feat, model, fmt, logits, s)
                                        : launch_features_k<kFeatCtasSmall, false>(c, rs, feat, model, fmt, logits, s));
-    SPMV_CUDA(e);
+    if (e != cudaSuccess) {
+        // the features kernel zeroes the slot after reading it; without it, zero it here
+        (void)cudaGetLastError();
+        (void)cudaMemsetAsync(rs, 0, sizeof(RowStatsSlot), s);
+        return cuda_error(e, "the features kernel's launch");
+    }
     return SPMV_OK;
 }
 
